@@ -1,0 +1,208 @@
+/*
+ * cmcg.h -- C ABI of the controllability method (CMCG) for time-harmonic
+ * Maxwell's equations on tetrahedral meshes, GB300 (sm_103a) implementation.
+ *
+ * Paper: T. Chaumont-Frelet, M. J. Grote, S. Lanteri, J. H. Tang, "A
+ * controllability method for Maxwell's equations", arXiv:2106.02858.
+ *
+ * Problem (Eq. maxwell_freq_strong / maxwell_time_strong): find complex (e, h)
+ * with  i w eps e + curl h = j,  i w mu h - curl e = 0  in Omega,
+ * e x n = 0 on the PEC part of the boundary and the first-order impedance
+ * (Silver-Mueller) condition on the rest.  CMCG (Section 2.2, Algorithms
+ * init / grad / cmcg) minimises J(U0) = 1/2 ||(I - P_w) U0 - G||^2 by
+ * conjugate gradients, where P_w advances the discontinuous-Galerkin
+ * time-domain scheme (Section 5.2.2, Eq. DG_semidiscrete / ode_system; RK2 or
+ * RK4, Algorithms rk2 / rk4) over one period T = 2 pi / w, P*_w is its
+ * discrete adjoint (Section 4.1.2) and the answer is the filtered field
+ * F_{psi,w} U0 = (2/T) int_0^T U(t) e^{-i w t} dt (Eq. filter_rhs, Section 5.4).
+ *
+ * ---------------------------------------------------------------------------
+ * Data layout at this boundary (all fields are double precision, row-major):
+ *
+ *   nodal field of one tetrahedron:   [component][node]
+ *   full field:                       [tet][component][node]
+ *     6 components for (E, H) = (Ex, Ey, Ez, Hx, Hy, Hz); 3 for e, h or j.
+ *   nodes of order q (Np = (q+1)(q+2)(q+3)/6): the equispaced lattice points
+ *     (i, j, k)/q, i, j, k >= 0, i + j + k <= q, of the unit tetrahedron
+ *     (0,0,0), (1,0,0), (0,1,0), (0,0,1), enumerated with k outermost, then j,
+ *     then i fastest; the physical node of tet (v0, v1, v2, v3) is
+ *     v0 + r (v1 - v0) + s (v2 - v0) + t (v3 - v0).
+ *   face f of a tetrahedron is the face opposite its vertex f.
+ *   face tags: 0 interior (must be shared by exactly two tetrahedra),
+ *              1 perfectly conducting, 2 impedance (Silver-Mueller, Z = sqrt(mu/eps)).
+ *
+ * Ownership: the caller owns every pointer it passes.  Inputs are copied (to
+ * the device) during the call; outputs are written before the call returns.
+ * The library owns the device state of a handle from cmcg_create to
+ * cmcg_destroy.  "_device" entry points take device pointers (same layout,
+ * double precision) and run on the handle's stream; they return once the
+ * work is complete (they synchronise the stream).
+ *
+ * Errors: every int-returning call returns CMCG_OK (0) on success, a
+ * negative CMCG_ERR_* code on failure (output buffers are then unspecified
+ * for device entry points and untouched for host entry points), or
+ * CMCG_NOT_CONVERGED (> 0) when cmcg_solve reached max_iter; its outputs are
+ * then valid (Algorithm cmcg returns the last iterate).
+ *
+ * Threading: one handle per host thread at a time.
+ */
+#ifndef CMCG_H
+#define CMCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum cmcg_status {
+  CMCG_OK = 0,
+  CMCG_NOT_CONVERGED = 1,
+  CMCG_ERR_INVALID_ARG = -1,
+  CMCG_ERR_NONCONFORMING_MESH = -2,
+  CMCG_ERR_OUT_OF_MEMORY = -3,
+  CMCG_ERR_UNSTABLE = -4,
+  CMCG_ERR_CG_BREAKDOWN = -5,
+  CMCG_ERR_NONFINITE = -6,
+  CMCG_ERR_DEVICE_TIMEOUT = -7,
+  CMCG_ERR_CUDA = -8,
+  CMCG_ERR_NO_DEVICE = -9
+};
+
+enum cmcg_precision { CMCG_FP64 = 0, CMCG_FP32 = 1 };
+enum cmcg_flux { CMCG_FLUX_UPWIND = 0, CMCG_FLUX_CENTRED = 1 };
+enum cmcg_tag { CMCG_TAG_INTERIOR = 0, CMCG_TAG_PEC = 1, CMCG_TAG_IMPEDANCE = 2 };
+
+/* A conforming tetrahedral mesh (Section 5.2.2).  verts: double[nv][3];
+ * tets: int32[nt][4] vertex indices; face_tags: uint8[nt][4]. */
+typedef struct cmcg_mesh {
+  int64_t nv;
+  const double* verts;
+  int64_t nt;
+  const int32_t* tets;
+  const uint8_t* face_tags;
+} cmcg_mesh;
+
+/* Options.  Fill with cmcg_default_options() first.
+ *   order:            polynomial degree q in {1, 2, 3}; q = 1 uses RK2 +
+ *                     trapezoid filter, q = 2, 3 use RK4 + Hermite filter
+ *                     (Section 5.3 / 5.4; q = 2 is not in the paper and is
+ *                     read as RK4 with c_2 = 0.12).
+ *   precision:        CMCG_FP64 or CMCG_FP32 for the time sweeps; CG
+ *                     scalars, dot products and the cost functional are FP64
+ *                     in both.
+ *   flux:             CMCG_FLUX_UPWIND (the paper's scheme) or
+ *                     CMCG_FLUX_CENTRED (energy-conserving, for tests).
+ *   c_q:              CFL constant of Eq. cfl; <= 0 selects 0.24 (q = 1),
+ *                     0.12 (q = 2, 3).
+ *   steps_per_period: > 0 forces M (dt = T / M) instead of the CFL choice.
+ *   hbm_budget_bytes: > 0 makes cmcg_create fail with
+ *                     CMCG_ERR_OUT_OF_MEMORY if the handle would need more
+ *                     device memory than this.
+ *   device:           CUDA device ordinal. */
+typedef struct cmcg_options {
+  int order;
+  int precision;
+  int flux;
+  int steps_per_period;
+  double c_q;
+  int64_t hbm_budget_bytes;
+  int device;
+  int reserved[7];
+} cmcg_options;
+
+/* Per-solve report. */
+typedef struct cmcg_info {
+  int iters;            /* CG iterations taken */
+  int periods;          /* periods simulated: 3 + 2 iters (Algorithms init, grad, final filter) */
+  int steps_per_period; /* M */
+  int status;           /* same as the return value */
+  double rel_residual;  /* ||R|| / ||R0|| in the (eps, mu) norm at exit */
+  double dt;            /* T / M */
+  double solve_ms;      /* wall time of the solve on the device */
+  double reserved[5];
+} cmcg_info;
+
+typedef struct cmcg_handle cmcg_handle;
+
+/* Fills *opt with: order 1, FP64, upwind, CFL choice, no budget, device 0. */
+void cmcg_default_options(cmcg_options* opt);
+
+/* Human-readable text for a status code (static storage). */
+const char* cmcg_status_string(int status);
+
+/* Host-only checks of a mesh and its data (no CUDA call): index ranges,
+ * non-degenerate tetrahedra, eps, mu > 0, omega > 0, order, tags, and
+ * conformity (every face shared by at most two tetrahedra, interior faces
+ * untagged, every unshared face tagged PEC or impedance, face nodes
+ * coincide).  Writes M (steps per period of Eq. cfl) to *steps if non-NULL. */
+int cmcg_validate(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
+                  const cmcg_options* opt, int* steps);
+
+/* Host-only: the reference matrices the library builds for order q (unit
+ * reference tetrahedron, boundary node order): mass[Np*Np], dr/ds/dt[Np*Np]
+ * (d phi_j / d r at node i, row i), lift[Np*4*Nfp] = M^{-1} times the face mass
+ * of each face (face f, face-node order = increasing volume node).  Any
+ * pointer may be NULL.  Returns CMCG_ERR_INVALID_ARG for q outside 1..3. */
+int cmcg_reference_matrices(int order, double* mass, double* dr, double* ds, double* dt, double* lift);
+
+/* Builds a handle: validates (as cmcg_validate), computes connectivity and
+ * geometry, chooses M (Eq. cfl), uploads the mesh in the device layout and
+ * allocates the CG state.  eps, mu: double[nt], element-constant, > 0. */
+int cmcg_create(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
+                const cmcg_options* opt, cmcg_handle** out);
+
+/* Releases the device state.  NULL is ignored. */
+void cmcg_destroy(cmcg_handle* h);
+
+/* Uses the given cudaStream_t (as void*) for all later work of the handle;
+ * NULL selects the legacy default stream. */
+int cmcg_set_stream(cmcg_handle* h, void* stream);
+
+/* Sizes of the handle: nt, Np, M (steps per period), dt, number of doubles of
+ * one full field (6 Np nt).  Any pointer may be NULL. */
+int cmcg_get_sizes(const cmcg_handle* h, int64_t* nt, int* np, int* steps, double* dt, int64_t* field_len);
+
+/* Phi(t, U) = Re(J e^{i w t}) + B U (Eq. ode_system), or Sigma B Sigma U when
+ * adjoint != 0 (no source then).  u, out: double[nt][6][Np]; j_re, j_im:
+ * double[nt][3][Np] current density (NULL = no source; j_im may be NULL). */
+int dgtd_apply(cmcg_handle* h, double t, const double* u, const double* j_re, const double* j_im, int adjoint,
+               double* out);
+
+/* One period forward (Section 4.1.2): uT = P_{psi,w} u0 with the source j
+ * (P_w if j_re is NULL).  If filt_re and filt_im are non-NULL they receive
+ * the filtered field F_{psi,w} u0 (Section 5.4), double[nt][6][Np] each. */
+int dgtd_period_forward(cmcg_handle* h, const double* u0, const double* j_re, const double* j_im, double* uT,
+                        double* filt_re, double* filt_im);
+
+/* One period of the discrete adjoint: w0 = P*_w wT = Sigma P_w Sigma wT
+ * (Lemma dual_propagators; the magnetic sign is flipped inside the kernels). */
+int dgtd_period_adjoint(cmcg_handle* h, const double* wT, double* w0);
+
+/* Device-pointer forms of the two sweeps (same layout, double). */
+int dgtd_period_forward_device(cmcg_handle* h, const double* u0, const double* j_re, const double* j_im, double* uT,
+                               double* filt_re, double* filt_im);
+int dgtd_period_adjoint_device(cmcg_handle* h, const double* wT, double* w0);
+
+/* The CMCG solve (Algorithm cmcg with Algorithms init and grad, initial
+ * guess 0, residual form) followed by the filter: (e, h) = F_{psi,w} U0.
+ * j_re, j_im: double[nt][3][Np] (j_im may be NULL); tol: stop when
+ * ||R|| <= tol ||R0|| in the (eps, mu) norm; max_iter >= 0.  e_re, e_im, h_re,
+ * h_im: double[nt][3][Np] each, caller-allocated.  info may be NULL. */
+int cmcg_solve(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
+               double* e_im, double* h_re, double* h_im, cmcg_info* info);
+
+/* Device-pointer form of cmcg_solve (same layout, double). */
+int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter,
+                      double* e_re, double* e_im, double* h_re, double* h_im, cmcg_info* info);
+
+/* Number of kernels the library launched on this handle since creation (a
+ * counter kept on the host at every launch). */
+int64_t cmcg_kernel_launches(const cmcg_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMCG_H */

@@ -1,0 +1,317 @@
+"""Python binding of libcmcg (ctypes; argument marshalling only).
+
+Every function has the name of the C entry point it wraps (``include/cmcg.h``)
+and does no arithmetic of its own: arrays are checked for dtype / shape /
+contiguity and their pointers passed through.  Host entry points take numpy
+arrays; ``*_device`` entry points take CUDA tensors (torch) whose
+``data_ptr()`` is passed, and run on the handle's stream (set with
+``cmcg_set_stream``).  If ``libcmcg.so`` is missing the import fails: there is
+no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcmcg.so")
+
+CMCG_OK = 0
+CMCG_NOT_CONVERGED = 1
+CMCG_ERR_INVALID_ARG = -1
+CMCG_ERR_NONCONFORMING_MESH = -2
+CMCG_ERR_OUT_OF_MEMORY = -3
+CMCG_ERR_UNSTABLE = -4
+CMCG_ERR_CG_BREAKDOWN = -5
+CMCG_ERR_NONFINITE = -6
+CMCG_ERR_DEVICE_TIMEOUT = -7
+CMCG_ERR_CUDA = -8
+CMCG_ERR_NO_DEVICE = -9
+CMCG_FP64, CMCG_FP32 = 0, 1
+CMCG_FLUX_UPWIND, CMCG_FLUX_CENTRED = 0, 1
+
+
+class cmcg_mesh(C.Structure):
+    _fields_ = [("nv", C.c_int64), ("verts", C.POINTER(C.c_double)), ("nt", C.c_int64),
+                ("tets", C.POINTER(C.c_int32)), ("face_tags", C.POINTER(C.c_uint8))]
+
+
+class cmcg_options(C.Structure):
+    _fields_ = [("order", C.c_int), ("precision", C.c_int), ("flux", C.c_int), ("steps_per_period", C.c_int),
+                ("c_q", C.c_double), ("hbm_budget_bytes", C.c_int64), ("device", C.c_int),
+                ("reserved", C.c_int * 7)]
+
+
+class cmcg_info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("periods", C.c_int), ("steps_per_period", C.c_int), ("status", C.c_int),
+                ("rel_residual", C.c_double), ("dt", C.c_double), ("solve_ms", C.c_double),
+                ("reserved", C.c_double * 5)]
+
+
+class CMCGError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {cmcg_status_string(code)} ({code})")
+        self.code = code
+
+
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+
+
+def _load() -> C.CDLL:
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libcmcg.so not built at {_LIB_PATH}; run paper_2106_02858_gb300/build.py "
+                          "(or __graft_entry__.build())")
+    lib = C.CDLL(_LIB_PATH)
+    sig = {
+        "cmcg_default_options": (None, [C.POINTER(cmcg_options)]),
+        "cmcg_status_string": (C.c_char_p, [C.c_int]),
+        "cmcg_validate": (C.c_int, [C.POINTER(cmcg_mesh), _dp, _dp, C.c_double, C.POINTER(cmcg_options),
+                                    C.POINTER(C.c_int)]),
+        "cmcg_reference_matrices": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp, _dp]),
+        "cmcg_create": (C.c_int, [C.POINTER(cmcg_mesh), _dp, _dp, C.c_double, C.POINTER(cmcg_options),
+                                  C.POINTER(_vp)]),
+        "cmcg_destroy": (None, [_vp]),
+        "cmcg_set_stream": (C.c_int, [_vp, _vp]),
+        "cmcg_get_sizes": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                     C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
+        "dgtd_apply": (C.c_int, [_vp, C.c_double, _dp, _dp, _dp, C.c_int, _dp]),
+        "dgtd_period_forward": (C.c_int, [_vp, _dp, _dp, _dp, _dp, _dp, _dp]),
+        "dgtd_period_adjoint": (C.c_int, [_vp, _dp, _dp]),
+        "dgtd_period_forward_device": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "dgtd_period_adjoint_device": (C.c_int, [_vp, _vp, _vp]),
+        "cmcg_solve": (C.c_int, [_vp, _dp, _dp, C.c_double, C.c_int, _dp, _dp, _dp, _dp, C.POINTER(cmcg_info)]),
+        "cmcg_solve_device": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp,
+                                        C.POINTER(cmcg_info)]),
+        "cmcg_kernel_launches": (C.c_int64, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg_reference_matrices", "cmcg_create",
+            "cmcg_destroy", "cmcg_set_stream", "cmcg_get_sizes", "dgtd_apply", "dgtd_period_forward",
+            "dgtd_period_adjoint", "dgtd_period_forward_device", "dgtd_period_adjoint_device", "cmcg_solve",
+            "cmcg_solve_device", "cmcg_kernel_launches")
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def _f64(a, shape=None, name="array"):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.size != int(np.prod(shape)):
+        raise ValueError(f"{name}: expected {shape} elements, got {a.shape}")
+    return a
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_dp)
+
+
+def _dev(t):
+    """data_ptr of a contiguous float64 CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype.itemsize == 8 and t.is_contiguous() and t.is_floating_point()):
+        raise ValueError("device arguments must be contiguous float64 CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _check(rc: int, where: str, allow_not_converged: bool = False) -> int:
+    if rc < 0 or (rc > 0 and not allow_not_converged):
+        raise CMCGError(rc, where)
+    return rc
+
+
+# ---------------------------------------------------------------------------------------------
+# Same-name wrappers.
+# ---------------------------------------------------------------------------------------------
+
+def cmcg_default_options(order: int = 1, precision: int = CMCG_FP64, flux: int = CMCG_FLUX_UPWIND,
+                         steps_per_period: int = 0, c_q: float = 0.0, hbm_budget_bytes: int = 0,
+                         device: int = 0) -> cmcg_options:
+    o = cmcg_options()
+    _lib.cmcg_default_options(C.byref(o))
+    o.order, o.precision, o.flux, o.steps_per_period = order, precision, flux, steps_per_period
+    o.c_q, o.hbm_budget_bytes, o.device = c_q, hbm_budget_bytes, device
+    return o
+
+
+def cmcg_status_string(code: int) -> str:
+    return _lib.cmcg_status_string(int(code)).decode()
+
+
+@dataclass
+class MeshArrays:
+    """Keeps the numpy arrays alive while a cmcg_mesh points at them."""
+
+    verts: np.ndarray
+    tets: np.ndarray
+    tags: np.ndarray
+    struct: cmcg_mesh
+
+
+def make_mesh(verts, tets, tags) -> MeshArrays:
+    v = np.ascontiguousarray(verts, dtype=np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    g = np.ascontiguousarray(tags, dtype=np.uint8).reshape(-1, 4)
+    if g.shape[0] != t.shape[0]:
+        raise ValueError("tags must have one row per tetrahedron")
+    m = cmcg_mesh(v.shape[0], v.ctypes.data_as(_dp), t.shape[0], t.ctypes.data_as(C.POINTER(C.c_int32)),
+                  g.ctypes.data_as(C.POINTER(C.c_uint8)))
+    return MeshArrays(v, t, g, m)
+
+
+def cmcg_validate(mesh: MeshArrays, eps, mu, omega: float, opt: cmcg_options):
+    """Returns (status, steps_per_period)."""
+    e, m = _f64(eps), _f64(mu)
+    steps = C.c_int(0)
+    rc = _lib.cmcg_validate(C.byref(mesh.struct), _ptr(e), _ptr(m), float(omega), C.byref(opt), C.byref(steps))
+    return rc, steps.value
+
+
+def cmcg_reference_matrices(order: int):
+    """(M, Dr, Ds, Dt, LIFT) of the library's reference element."""
+    np_ = (order + 1) * (order + 2) * (order + 3) // 6
+    nfp = (order + 1) * (order + 2) // 2
+    M, Dr, Ds, Dt = (np.zeros((np_, np_)) for _ in range(4))
+    L = np.zeros((np_, 4 * nfp))
+    _check(_lib.cmcg_reference_matrices(order, _ptr(M), _ptr(Dr), _ptr(Ds), _ptr(Dt), _ptr(L)),
+           "cmcg_reference_matrices")
+    return M, Dr, Ds, Dt, L
+
+
+class Handle:
+    """Owns a cmcg_handle (cmcg_create / cmcg_destroy)."""
+
+    def __init__(self, ptr: int, nt: int, np_: int, steps: int, dt: float):
+        self.ptr = C.c_void_p(ptr)
+        self.nt, self.np, self.steps, self.dt = nt, np_, steps, dt
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            _lib.cmcg_destroy(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def cmcg_create(mesh: MeshArrays, eps, mu, omega: float, opt: cmcg_options) -> Handle:
+    e, m = _f64(eps), _f64(mu)
+    out = C.c_void_p()
+    _check(_lib.cmcg_create(C.byref(mesh.struct), _ptr(e), _ptr(m), float(omega), C.byref(opt), C.byref(out)),
+           "cmcg_create")
+    nt, np_, steps, dt, fl = C.c_int64(), C.c_int(), C.c_int(), C.c_double(), C.c_int64()
+    _check(_lib.cmcg_get_sizes(out, C.byref(nt), C.byref(np_), C.byref(steps), C.byref(dt), C.byref(fl)),
+           "cmcg_get_sizes")
+    return Handle(out.value, nt.value, np_.value, steps.value, dt.value)
+
+
+def cmcg_destroy(h: Handle) -> None:
+    h.close()
+
+
+def cmcg_set_stream(h: Handle, stream) -> None:
+    """``stream``: a torch.cuda.Stream, a raw cudaStream_t int, or None."""
+    raw = getattr(stream, "cuda_stream", stream)
+    _check(_lib.cmcg_set_stream(h.ptr, C.c_void_p(raw) if raw else None), "cmcg_set_stream")
+
+
+def cmcg_get_sizes(h: Handle):
+    nt, np_, steps, dt, fl = C.c_int64(), C.c_int(), C.c_int(), C.c_double(), C.c_int64()
+    _check(_lib.cmcg_get_sizes(h.ptr, C.byref(nt), C.byref(np_), C.byref(steps), C.byref(dt), C.byref(fl)),
+           "cmcg_get_sizes")
+    return nt.value, np_.value, steps.value, dt.value, fl.value
+
+
+def cmcg_kernel_launches(h: Handle) -> int:
+    return int(_lib.cmcg_kernel_launches(h.ptr))
+
+
+def _field(h: Handle, u, ncomp=6, name="field"):
+    return _f64(u, (h.nt, ncomp, h.np), name)
+
+
+def dgtd_apply(h: Handle, t: float, u, j_re=None, j_im=None, adjoint: bool = False) -> np.ndarray:
+    u = _field(h, u, 6, "u")
+    jr, ji = _field(h, j_re, 3, "j_re"), _field(h, j_im, 3, "j_im")
+    out = np.empty((h.nt, 6, h.np))
+    _check(_lib.dgtd_apply(h.ptr, float(t), _ptr(u), _ptr(jr), _ptr(ji), int(bool(adjoint)), _ptr(out)),
+           "dgtd_apply")
+    return out
+
+
+def dgtd_period_forward(h: Handle, u0, j_re=None, j_im=None, filtered: bool = False):
+    """Returns uT, or (uT, filt_re, filt_im) when ``filtered``."""
+    u0 = _field(h, u0, 6, "u0")
+    jr, ji = _field(h, j_re, 3, "j_re"), _field(h, j_im, 3, "j_im")
+    uT = np.empty((h.nt, 6, h.np))
+    fr = np.empty_like(uT) if filtered else None
+    fi = np.empty_like(uT) if filtered else None
+    _check(_lib.dgtd_period_forward(h.ptr, _ptr(u0), _ptr(jr), _ptr(ji), _ptr(uT), _ptr(fr), _ptr(fi)),
+           "dgtd_period_forward")
+    return (uT, fr, fi) if filtered else uT
+
+
+def dgtd_period_adjoint(h: Handle, wT) -> np.ndarray:
+    wT = _field(h, wT, 6, "wT")
+    w0 = np.empty((h.nt, 6, h.np))
+    _check(_lib.dgtd_period_adjoint(h.ptr, _ptr(wT), _ptr(w0)), "dgtd_period_adjoint")
+    return w0
+
+
+def dgtd_period_forward_device(h: Handle, u0, j_re, j_im, uT, filt_re=None, filt_im=None) -> None:
+    _check(_lib.dgtd_period_forward_device(h.ptr, _dev(u0), _dev(j_re), _dev(j_im), _dev(uT), _dev(filt_re),
+                                           _dev(filt_im)), "dgtd_period_forward_device")
+
+
+def dgtd_period_adjoint_device(h: Handle, wT, w0) -> None:
+    _check(_lib.dgtd_period_adjoint_device(h.ptr, _dev(wT), _dev(w0)), "dgtd_period_adjoint_device")
+
+
+def cmcg_solve(h: Handle, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 1000):
+    """Returns (e, h_field, info) with e, h complex (nt, 3, Np)."""
+    jr, ji = _field(h, j_re, 3, "j_re"), _field(h, j_im, 3, "j_im")
+    er, ei, hr, hi = (np.empty((h.nt, 3, h.np)) for _ in range(4))
+    info = cmcg_info()
+    _check(_lib.cmcg_solve(h.ptr, _ptr(jr), _ptr(ji), float(tol), int(max_iter), _ptr(er), _ptr(ei), _ptr(hr),
+                           _ptr(hi), C.byref(info)), "cmcg_solve", allow_not_converged=True)
+    return er + 1j * ei, hr + 1j * hi, info
+
+
+def cmcg_solve_device(h: Handle, j_re, j_im, tol: float, max_iter: int, e_re, e_im, h_re, h_im) -> cmcg_info:
+    info = cmcg_info()
+    _check(_lib.cmcg_solve_device(h.ptr, _dev(j_re), _dev(j_im), float(tol), int(max_iter), _dev(e_re), _dev(e_im),
+                                  _dev(h_re), _dev(h_im), C.byref(info)), "cmcg_solve_device",
+           allow_not_converged=True)
+    return info
+
+
+def create_for_problem(problem, precision: int = CMCG_FP64, flux: int = CMCG_FLUX_UPWIND, steps_per_period: int = 0,
+                       device: int = 0, hbm_budget_bytes: int = 0):
+    """Convenience: cmcg_create from an ``inputs.Problem``; returns (handle, mesh arrays)."""
+    mesh = make_mesh(problem.mesh.verts, problem.mesh.tets, problem.mesh.tags)
+    opt = cmcg_default_options(order=problem.order, precision=precision, flux=flux,
+                               steps_per_period=steps_per_period, device=device, hbm_budget_bytes=hbm_budget_bytes)
+    return cmcg_create(mesh, problem.eps, problem.mu, problem.omega, opt), mesh

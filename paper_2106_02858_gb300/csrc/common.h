@@ -1,0 +1,166 @@
+// Internal declarations of libcmcg (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cmcg.h"
+
+namespace cmcg {
+
+constexpr int TILE = 32;  // tetrahedra per tile = lanes of a warp
+
+constexpr int np_of(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
+constexpr int nfp_of(int q) { return (q + 1) * (q + 2) / 2; }
+
+// Face f is opposite vertex f; its vertices in this order (face-local vertex s = 0, 1, 2).
+constexpr int FACE_VERTS[4][3] = {{1, 2, 3}, {0, 2, 3}, {0, 1, 3}, {0, 1, 2}};
+
+// The six permutations sigma of {0,1,2}: face-local vertex s of a tetrahedron is
+// face-local vertex sigma[s] of its neighbour across that face.
+constexpr int PERMS[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+// Index of lattice node (i, j, k) of order q in boundary order (k outermost, i fastest).
+constexpr int lattice_index(int q, int i, int j, int k) {
+  int idx = 0;
+  for (int kk = 0; kk < k; ++kk) idx += (q - kk + 1) * (q - kk + 2) / 2;
+  for (int jj = 0; jj < j; ++jj) idx += q - k - jj + 1;
+  return idx + i;
+}
+
+// Volume node of face-local node jf of face f.  Face-local nodes enumerate the
+// barycentric weights (w0, w1, w2) over the face's vertices with w2 outermost,
+// w1 fastest, w0 = q - w1 - w2.
+struct FaceTab {
+  int v[4][10];
+};
+constexpr FaceTab make_fmask(int q) {
+  FaceTab t{};
+  for (int f = 0; f < 4; ++f) {
+    int jf = 0;
+    for (int w2 = 0; w2 <= q; ++w2)
+      for (int w1 = 0; w1 <= q - w2; ++w1) {
+        int b[4] = {0, 0, 0, 0};
+        b[FACE_VERTS[f][0]] = q - w1 - w2;
+        b[FACE_VERTS[f][1]] = w1;
+        b[FACE_VERTS[f][2]] = w2;
+        t.v[f][jf++] = lattice_index(q, b[1], b[2], b[3]);
+      }
+  }
+  return t;
+}
+
+// Reference element of order q on the unit tetrahedron, built from a monomial
+// basis and exact simplex integrals (host, double).
+struct RefMats {
+  int q = 0, np = 0, nfp = 0;
+  std::vector<double> M, Minv, Dr, Ds, Dt;  // np x np, row-major
+  std::vector<double> LIFT;                 // np x (4 nfp), face-local node order
+  std::vector<int> fmask;                   // 4 x nfp
+  std::vector<int> nbrnode;                 // 4 (neighbour face) x 6 (perm) x nfp
+  double face_ref_area[4] = {0, 0, 0, 0};
+};
+const RefMats& ref_mats(int q);
+
+// Per-tetrahedron geometry in the device layout, built on the host.
+struct HostLayout {
+  int q = 0, np = 0;
+  int64_t nt = 0, nti = 0, ntiles = 0;
+  std::vector<int32_t> ext_of_int;  // internal -> external tet (-1 = padding)
+  std::vector<int32_t> int_of_ext;  // external -> internal
+  std::vector<double> gvol;         // [tile][GV][32]
+  std::vector<double> gface;        // [tile][4][GF][32]
+  std::vector<int32_t> nbr;         // [tile][4][32]
+  std::vector<double> wdot;         // [tile][2][32]: |det| eps, |det| mu
+  int steps = 0;
+  double dt = 0, T = 0, rho_min = 0;
+  int ngroups = 0;
+};
+constexpr int GV = 12;  // G (9, d r_b / d x_a at [b*3+a]), 1/eps, 1/mu, pad
+constexpr int GF = 8;   // nx, ny, nz, aE, bE, aH, bH, pad
+
+int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
+                        const cmcg_options* opt, HostLayout* out, bool build_layout, std::string* why);
+
+// Neighbour code: >= 0: (internal neighbour << 5) | (neighbour face << 3) | perm.
+constexpr int32_t NBR_PEC = -1;
+constexpr int32_t NBR_IMP = -2;
+
+// Arguments of one RK stage over all tetrahedra.
+//   Phi   = src + B_sigma(vin)      (B_sigma = Sigma B Sigma when sH = -1)
+//   out   = base + c_out Phi        (skipped if out == nullptr)
+//   acc_o = acc_i + c_acc Phi       (skipped if acc_o == nullptr)
+//   F    += fa vin + fb Phi         (complex weights; skipped if fre == nullptr)
+template <typename R>
+struct StageArgs {
+  const R* vin;
+  const R* base;
+  R* out;
+  R c_out;
+  const R* acc_in;
+  R* acc_out;
+  R c_acc;
+  const R* jre;  // E-rows source / eps, [tile][3][Np][32]
+  const R* jim;
+  R s_cos, s_sin;  // Re(J e^{iwt}) = jre cos - jim sin
+  R* fre;
+  R* fim;
+  R fa_re, fa_im, fb_re, fb_im;
+  R sH;  // +1 forward, -1 adjoint
+  const R* gvol;
+  const R* gface;
+  const int32_t* nbr;
+  int64_t nti;
+};
+
+// Kernel launchers, one translation unit per order.
+template <int Q, typename R>
+void launch_stage(const StageArgs<R>& a, cudaStream_t s);
+template <int Q>
+void upload_constants(const RefMats& rm);
+
+// Vector kernels (vec.cu).
+struct Scalars {
+  double rr, rr_new, dA, alpha, beta, rr0;
+  int status;
+  int pad;
+};
+
+// Layout conversion over (tet, c in [0, cnt), node):
+//   internal [tile][ncomp_in][np][32] at component c_in0 + c  <->  external [tet][ncomp_ext][np] at c_ext0 + c.
+// to_internal multiplies by scale (and by per_tet[e] if non-null); padding tets get 0.
+template <typename R>
+void launch_to_internal(const double* ext, int ncomp_ext, int c_ext0, R* in, int ncomp_in, int c_in0, int cnt,
+                        const int32_t* ext_of_int, int64_t nti, int np, double scale, const double* per_tet,
+                        cudaStream_t s);
+template <typename R>
+void launch_to_external(const R* in, int ncomp_in, int c_in0, double* ext, int ncomp_ext, int c_ext0, int cnt,
+                        const int32_t* ext_of_int, int64_t nti, int np, cudaStream_t s);
+// o1 = o2 = o3 = a x + b y (null outputs skipped, y may be null).
+template <typename R>
+void launch_lincomb3(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n, cudaStream_t s);
+
+// M-weighted dot products and CG updates (vec.cu); Q-dispatched internally.
+template <typename R>
+void launch_cg_after_adjoint(int q, const R* Uw, const R* WT, R* A, const R* D, const double* wdot, double* partials,
+                             int64_t nti, cudaStream_t s);
+template <typename R>
+void launch_cg_update(int q, R* U0, R* Rv, const R* D, const R* A, const double* wdot, const Scalars* sc,
+                      double* partials, int64_t nti, cudaStream_t s);
+template <typename R>
+void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* partials, int64_t nti, cudaStream_t s);
+template <typename R>
+void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, int64_t n, cudaStream_t s);
+
+int dot_blocks(int64_t nti);
+// which: 0 -> rr (and rr0), 1 -> dA (then alpha = rr / dA), 2 -> rr_new (then beta), 3 -> generic into rr_new
+void launch_finalize(double* partials, int nblocks, Scalars* sc, int which, cudaStream_t s);
+void upload_dot_mass(int q, const double* M);
+
+// Gauss-Legendre rule on [0, 1] (refelem.cpp).
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+
+}  // namespace cmcg

@@ -1,0 +1,305 @@
+// Vector kernels of the CMCG outer loop (Section 2.2, Algorithm cmcg):
+// layout conversion between the boundary layout [tet][comp][node] (double) and
+// the device layout [tile][comp][node][lane], fused CG updates, and the
+// (eps, mu)-weighted inner product (Eq. innerproduct)
+//     (X, Y) = sum_K |det A_K| sum_c w_c sum_ij X_c[i] Mref[i][j] Y_c[j],
+// w_c = eps_K on E rows, mu_K on H rows, accumulated in FP64 whatever the
+// storage precision.  Reductions are deterministic: one partial per block
+// (warp shuffles, then shared memory in a fixed order) and one finalising
+// block that sums the partials in a fixed order.
+#include "common.h"
+
+namespace cmcg {
+namespace {
+
+constexpr int DOT_THREADS = 128;
+constexpr int DOT_MAX_BLOCKS = 4096;
+
+__constant__ double cM1[4 * 4];
+__constant__ double cM2[10 * 10];
+__constant__ double cM3[20 * 20];
+
+template <int Q>
+__device__ __forceinline__ double cM(int idx) {
+  if constexpr (Q == 1) return cM1[idx];
+  else if constexpr (Q == 2) return cM2[idx];
+  else return cM3[idx];
+}
+
+template <typename R>
+__global__ void to_internal_kernel(const double* __restrict__ ext, int ncomp_ext, int c_ext0, R* __restrict__ in,
+                                   int ncomp_in, int c_in0, int cnt, const int32_t* __restrict__ e_of_i, int64_t nti,
+                                   int np, double scale, const double* __restrict__ per_tet) {
+  const int64_t total = nti * cnt * np;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = int(idx % TILE);
+    const int64_t r = idx / TILE;
+    const int n = int(r % np);
+    const int c = int((r / np) % cnt);
+    const int64_t tile = r / ((int64_t)np * cnt);
+    const int32_t e = e_of_i[tile * TILE + lane];
+    R v = R(0);
+    if (e >= 0) {
+      double x = ext[((int64_t)e * ncomp_ext + c_ext0 + c) * np + n] * scale;
+      if (per_tet) x *= per_tet[e];
+      v = R(x);
+    }
+    in[((tile * ncomp_in + c_in0 + c) * np + n) * TILE + lane] = v;
+  }
+}
+
+template <typename R>
+__global__ void to_external_kernel(const R* __restrict__ in, int ncomp_in, int c_in0, double* __restrict__ ext,
+                                   int ncomp_ext, int c_ext0, int cnt, const int32_t* __restrict__ e_of_i, int64_t nti,
+                                   int np) {
+  const int64_t total = nti * cnt * np;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int lane = int(idx % TILE);
+    const int64_t r = idx / TILE;
+    const int n = int(r % np);
+    const int c = int((r / np) % cnt);
+    const int64_t tile = r / ((int64_t)np * cnt);
+    const int32_t e = e_of_i[tile * TILE + lane];
+    if (e >= 0) ext[((int64_t)e * ncomp_ext + c_ext0 + c) * np + n] = double(in[((tile * ncomp_in + c_in0 + c) * np + n) * TILE + lane]);
+  }
+}
+
+template <typename R>
+__global__ void lincomb_kernel(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = a * double(x[i]);
+    if (y) v += b * double(y[i]);
+    const R r = R(v);
+    if (o1) o1[i] = r;
+    if (o2) o2[i] = r;
+    if (o3) o3[i] = r;
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double sh[DOT_THREADS / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < DOT_THREADS / 32; ++i) s += sh[i];
+  return s;
+}
+
+// Per-tet weighted dot of X and Y (vectors in device layout).
+template <int Q, typename R>
+__device__ __forceinline__ double tet_dot(const R* X, const R* Y, int64_t tile, int lane, const double* wdot) {
+  constexpr int NP = np_of(Q);
+  const R* x = X + tile * (6 * NP * TILE) + lane;
+  const R* y = Y + tile * (6 * NP * TILE) + lane;
+  const double wE = wdot[(tile * 2 + 0) * TILE + lane], wH = wdot[(tile * 2 + 1) * TILE + lane];
+  double total = 0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    double yv[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) yv[j] = double(y[(c * NP + j) * TILE]);
+    double s = 0;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      double t = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) t = fma(cM<Q>(i * NP + j), yv[j], t);
+      s = fma(double(x[(c * NP + i) * TILE]), t, s);
+    }
+    total += (c < 3 ? wE : wH) * s;
+  }
+  return total;
+}
+
+// A = Uw - WT; partial (D, A).
+template <int Q, typename R>
+__global__ void __launch_bounds__(DOT_THREADS) cg_after_adjoint_kernel(const R* Uw, const R* WT, R* A, const R* D,
+                                                                      const double* wdot, double* partials, int64_t nti) {
+  constexpr int NP = np_of(Q);
+  double acc = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nti; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = t >> 5;
+    const int lane = int(t & 31);
+    const int64_t base = tile * (6 * NP * TILE) + lane;
+#pragma unroll
+    for (int k = 0; k < 6 * NP; ++k) A[base + k * TILE] = R(double(Uw[base + k * TILE]) - double(WT[base + k * TILE]));
+    acc += tet_dot<Q, R>(D, A, tile, lane, wdot);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// U0 += alpha D; R -= alpha A; partial (R, R).
+template <int Q, typename R>
+__global__ void __launch_bounds__(DOT_THREADS) cg_update_kernel(R* U0, R* Rv, const R* D, const R* A, const double* wdot,
+                                                               const Scalars* sc, double* partials, int64_t nti) {
+  constexpr int NP = np_of(Q);
+  const double alpha = sc->alpha;
+  double acc = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nti; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t tile = t >> 5;
+    const int lane = int(t & 31);
+    const int64_t base = tile * (6 * NP * TILE) + lane;
+#pragma unroll
+    for (int k = 0; k < 6 * NP; ++k) {
+      const int64_t o = base + k * TILE;
+      U0[o] = R(double(U0[o]) + alpha * double(D[o]));
+      Rv[o] = R(double(Rv[o]) - alpha * double(A[o]));
+    }
+    acc += tet_dot<Q, R>(Rv, Rv, tile, lane, wdot);
+  }
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <int Q, typename R>
+__global__ void __launch_bounds__(DOT_THREADS) dot_kernel(const R* X, const R* Y, const double* wdot, double* partials,
+                                                         int64_t nti) {
+  double acc = 0;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nti; t += (int64_t)gridDim.x * blockDim.x)
+    acc += tet_dot<Q, R>(X, Y, t >> 5, int(t & 31), wdot);
+  const double s = block_sum(acc);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// D = R + beta D; Uw = D.
+template <typename R>
+__global__ void cg_direction_kernel(R* D, R* Uw, const R* Rv, const Scalars* sc, int64_t n) {
+  const double beta = sc->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const R v = R(double(Rv[i]) + beta * double(D[i]));
+    D[i] = v;
+    Uw[i] = v;
+  }
+}
+
+__global__ void finalize_kernel(const double* partials, int nblocks, Scalars* sc, int which) {
+  __shared__ double sh[256];
+  double s = 0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += partials[i];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double tot = sh[0];
+    if (!isfinite(tot)) sc->status = CMCG_ERR_NONFINITE;
+    if (which == 0) {
+      sc->rr = tot;
+      sc->rr0 = tot;
+    } else if (which == 1) {
+      sc->dA = tot;
+      if (!(tot > 0)) {
+        if (sc->status == 0) sc->status = CMCG_ERR_CG_BREAKDOWN;
+        sc->alpha = 0;
+      } else {
+        sc->alpha = sc->rr / tot;
+      }
+    } else if (which == 2) {
+      sc->rr_new = tot;
+      sc->beta = sc->rr > 0 ? tot / sc->rr : 0.0;
+      sc->rr = tot;
+    } else {
+      sc->rr_new = tot;
+    }
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t b = (n + threads - 1) / threads;
+  if (b > 152 * 64) b = 152 * 64;
+  if (b < 1) b = 1;
+  return int(b);
+}
+
+}  // namespace
+
+int dot_blocks(int64_t nti) {
+  int64_t b = (nti + DOT_THREADS - 1) / DOT_THREADS;
+  if (b > DOT_MAX_BLOCKS) b = DOT_MAX_BLOCKS;
+  if (b < 1) b = 1;
+  return int(b);
+}
+
+void upload_dot_mass(int q, const double* M) {
+  const int np = np_of(q);
+  if (q == 1) cudaMemcpyToSymbol(cM1, M, sizeof(double) * np * np);
+  else if (q == 2) cudaMemcpyToSymbol(cM2, M, sizeof(double) * np * np);
+  else cudaMemcpyToSymbol(cM3, M, sizeof(double) * np * np);
+}
+
+template <typename R>
+void launch_to_internal(const double* ext, int ncomp_ext, int c_ext0, R* in, int ncomp_in, int c_in0, int cnt,
+                        const int32_t* e_of_i, int64_t nti, int np, double scale, const double* per_tet, cudaStream_t s) {
+  const int64_t n = nti * cnt * np;
+  to_internal_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(ext, ncomp_ext, c_ext0, in, ncomp_in, c_in0, cnt, e_of_i, nti,
+                                                         np, scale, per_tet);
+}
+template <typename R>
+void launch_to_external(const R* in, int ncomp_in, int c_in0, double* ext, int ncomp_ext, int c_ext0, int cnt,
+                        const int32_t* e_of_i, int64_t nti, int np, cudaStream_t s) {
+  const int64_t n = nti * cnt * np;
+  to_external_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(in, ncomp_in, c_in0, ext, ncomp_ext, c_ext0, cnt, e_of_i, nti,
+                                                         np);
+}
+template <typename R>
+void launch_lincomb3(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n, cudaStream_t s) {
+  lincomb_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(o1, o2, o3, a, x, b, y, n);
+}
+
+#define CMCG_DISPATCH_Q(q, KERNEL, ...)                                       \
+  do {                                                                        \
+    if ((q) == 1) KERNEL<1, R><<<nb, DOT_THREADS, 0, s>>>(__VA_ARGS__);       \
+    else if ((q) == 2) KERNEL<2, R><<<nb, DOT_THREADS, 0, s>>>(__VA_ARGS__);  \
+    else KERNEL<3, R><<<nb, DOT_THREADS, 0, s>>>(__VA_ARGS__);                \
+  } while (0)
+
+template <typename R>
+void launch_cg_after_adjoint(int q, const R* Uw, const R* WT, R* A, const R* D, const double* wdot, double* partials,
+                             int64_t nti, cudaStream_t s) {
+  const int nb = dot_blocks(nti);
+  CMCG_DISPATCH_Q(q, cg_after_adjoint_kernel, Uw, WT, A, D, wdot, partials, nti);
+}
+template <typename R>
+void launch_cg_update(int q, R* U0, R* Rv, const R* D, const R* A, const double* wdot, const Scalars* sc,
+                      double* partials, int64_t nti, cudaStream_t s) {
+  const int nb = dot_blocks(nti);
+  CMCG_DISPATCH_Q(q, cg_update_kernel, U0, Rv, D, A, wdot, sc, partials, nti);
+}
+template <typename R>
+void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* partials, int64_t nti, cudaStream_t s) {
+  const int nb = dot_blocks(nti);
+  CMCG_DISPATCH_Q(q, dot_kernel, X, Y, wdot, partials, nti);
+}
+template <typename R>
+void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, int64_t n, cudaStream_t s) {
+  cg_direction_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(D, Uw, Rv, sc, n);
+}
+void launch_finalize(double* partials, int nblocks, Scalars* sc, int which, cudaStream_t s) {
+  finalize_kernel<<<1, 256, 0, s>>>(partials, nblocks, sc, which);
+}
+
+#define CMCG_INST(R)                                                                                                  \
+  template void launch_to_internal<R>(const double*, int, int, R*, int, int, int, const int32_t*, int64_t, int,        \
+                                      double, const double*, cudaStream_t);                                           \
+  template void launch_to_external<R>(const R*, int, int, double*, int, int, int, const int32_t*, int64_t, int,       \
+                                      cudaStream_t);                                                                  \
+  template void launch_lincomb3<R>(R*, R*, R*, double, const R*, double, const R*, int64_t, cudaStream_t);             \
+  template void launch_cg_after_adjoint<R>(int, const R*, const R*, R*, const R*, const double*, double*, int64_t,     \
+                                           cudaStream_t);                                                             \
+  template void launch_cg_update<R>(int, R*, R*, const R*, const R*, const double*, const Scalars*, double*, int64_t, \
+                                    cudaStream_t);                                                                    \
+  template void launch_dot<R>(int, const R*, const R*, const double*, double*, int64_t, cudaStream_t);               \
+  template void launch_cg_direction<R>(R*, R*, const R*, const Scalars*, int64_t, cudaStream_t);
+CMCG_INST(float)
+CMCG_INST(double)
+
+}  // namespace cmcg

@@ -1,0 +1,143 @@
+"""Host-side checks of libcmcg that need no GPU.
+
+* The library loads and exports every function that ``include/cmcg.h`` declares.
+* ``cmcg_validate`` rejects broken meshes and computes the same number of
+  steps per period (Eq. cfl) as the oracle, bit for bit.
+* ``cmcg_reference_matrices`` (monomial basis, exact simplex integrals, Duffy
+  quadrature on the unit tetrahedron) equals the oracle's Dubiner-based
+  matrices after the change of reference tetrahedron.
+* Without a GPU, ``cmcg_create`` fails cleanly with CMCG_ERR_NO_DEVICE.
+* The product package never imports the oracle.
+"""
+import ast
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2106_02858_gb300 import build
+    build.build()
+    from paper_2106_02858_gb300 import cmcg
+    return cmcg
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "cmcg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_function(lib):
+    names = _declared_functions()
+    assert len(names) >= 15
+    out = subprocess.run(["nm", "-D", "--defined-only", lib.library_path()], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    assert set(lib.EXPORTED) == set(names)
+
+
+def _mesh(n=2):
+    from paper_2106_02858_gb300 import inputs as I
+    return I.kuhn_cube_mesh(n)
+
+
+def test_validate_rejects_broken_meshes(lib):
+    m = _mesh()
+    eps, mu = np.ones(m.nt), np.ones(m.nt)
+    opt = lib.cmcg_default_options(order=1)
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, 2 * np.pi, opt)[0] == lib.CMCG_OK
+    tags = m.tags.copy()
+    tags[0, 1] = 1  # boundary tag on an interior face
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, tags), eps, mu, 2 * np.pi, opt)[0] == \
+        lib.CMCG_ERR_NONCONFORMING_MESH
+    tags = m.tags.copy()
+    b = np.argwhere(tags > 0)[0]
+    tags[b[0], b[1]] = 0  # unmatched face without tag
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, tags), eps, mu, 2 * np.pi, opt)[0] == \
+        lib.CMCG_ERR_NONCONFORMING_MESH
+    tets = np.concatenate([m.tets, m.tets[:1]])  # a duplicated tetrahedron: faces shared three times
+    tg = np.concatenate([m.tags, m.tags[:1]])
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, tets, tg), np.ones(m.nt + 1), np.ones(m.nt + 1), 2 * np.pi,
+                             opt)[0] == lib.CMCG_ERR_NONCONFORMING_MESH
+    bad = m.tets.copy()
+    bad[0, 1] = bad[0, 0]
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, bad, m.tags), eps, mu, 2 * np.pi, opt)[0] == lib.CMCG_ERR_INVALID_ARG
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), -eps, mu, 2 * np.pi, opt)[0] == \
+        lib.CMCG_ERR_INVALID_ARG
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, -1.0, opt)[0] == lib.CMCG_ERR_INVALID_ARG
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, 1.0,
+                             lib.cmcg_default_options(order=4))[0] == lib.CMCG_ERR_INVALID_ARG
+    tags = m.tags.copy()
+    tags[0, 0] = 7
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, tags), eps, mu, 1.0, opt)[0] == lib.CMCG_ERR_INVALID_ARG
+    flat = m.verts.copy()
+    flat[:, 2] = 0.0  # every tetrahedron degenerate
+    assert lib.cmcg_validate(lib.make_mesh(flat, m.tets, m.tags), eps, mu, 1.0, opt)[0] == lib.CMCG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("which", ["plain", "scatterer", "batched", "uneven"])
+def test_steps_per_period_match_oracle(lib, which):
+    from paper_2106_02858_gb300 import inputs as I
+    from oracle.geometry import build_geometry
+    from oracle.timestep import steps_per_period
+    p = {"plain": I.plain_fp64_cube, "scatterer": I.scatterer_sphere, "batched": lambda: I.batched_rhs(nrhs=1),
+         "uneven": lambda: I.uneven_batch(count=3)[2]}[which]()
+    rc, M = lib.cmcg_validate(lib.make_mesh(p.mesh.verts, p.mesh.tets, p.mesh.tags), p.eps, p.mu, p.omega,
+                              lib.cmcg_default_options(order=p.order))
+    assert rc == lib.CMCG_OK
+    g = build_geometry(p.mesh.verts, p.mesh.tets, p.mesh.tags, p.eps, p.mu, p.order)
+    assert M == steps_per_period(g, p.omega)
+
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+def test_reference_matrices_match_oracle(lib, q):
+    from oracle.refelem import ref_element
+    M, Dr, Ds, Dt, L = lib.cmcg_reference_matrices(q)
+    R = ref_element(q)
+    # unit tet x = (r + 1) / 2: d/dx = 2 d/dr, dV_unit = dV_biunit / 8
+    assert np.allclose(M, R.M / 8, atol=1e-14)
+    assert np.allclose(Dr, 2 * R.Dr, atol=1e-11)
+    assert np.allclose(Ds, 2 * R.Ds, atol=1e-11)
+    assert np.allclose(Dt, 2 * R.Dt, atol=1e-11)
+    # library face masses use the unit-tet face areas; the oracle's use area-2 reference triangles
+    area = [np.sqrt(3) / 2, 0.5, 0.5, 0.5]
+    nfp = R.Nfp
+    for f in range(4):
+        assert np.allclose(L[:, f * nfp:(f + 1) * nfp], 4 * area[f] * R.LIFT[:, f * nfp:(f + 1) * nfp], atol=1e-11)
+
+
+def test_create_without_gpu_fails_cleanly(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    m = _mesh()
+    with pytest.raises(lib.CMCGError) as ei:
+        lib.cmcg_create(lib.make_mesh(m.verts, m.tets, m.tags), np.ones(m.nt), np.ones(m.nt), 1.0,
+                        lib.cmcg_default_options())
+    assert ei.value.code in (lib.CMCG_ERR_NO_DEVICE, lib.CMCG_ERR_CUDA)
+
+
+def test_product_package_never_imports_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2106_02858_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith(".py"):
+                tree = ast.parse(open(os.path.join(dirpath, f)).read())
+                for node in ast.walk(tree):
+                    if isinstance(node, (ast.Import, ast.ImportFrom)):
+                        mods = [a.name for a in node.names] if isinstance(node, ast.Import) else [node.module or ""]
+                        assert not any(m.split(".")[0] == "oracle" for m in mods), (f, mods)
+    # and the oracle only takes the seeded input generators from the package
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith(".py"):
+            src = open(os.path.join(ROOT, "oracle", f)).read()
+            for mod in re.findall(r"from (paper_2106_02858_gb300[\w.]*) import", src):
+                assert mod == "paper_2106_02858_gb300.inputs", (f, mod)
