@@ -1,0 +1,396 @@
+#!/usr/bin/env python
+"""Benchmark of the CMCG hot path on one GB300 (or N replicas under torchrun).
+
+Workload: the 24^3-cube Kuhn mesh minus a centred PEC cube of side 0.25
+(81,648 tetrahedra), nodal P2 (4,898,880 dofs), eps = 4 in a seeded sphere of
+radius 0.15, impedance outer boundary, omega = 4 pi (242 RK4 steps per period),
+seeded Gaussian source.  A step is one complete CMCG solve (Algorithms init,
+grad, cmcg and the final filter) with FP32 sweeps and FP64 CG scalars, to a
+relative CG residual of 1e-5; its filtered result is compared with the FP64
+solve of the same problem in the same run.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CMCG solves/s at 1e-4 rel. L2 vs FP64 plain; DG dof-updates/s; p50/p99 latency"
+UNIT = "solves/s"
+CG_TOL = 1e-5
+MAX_ITER = 2000
+WORKLOAD = ("scatterer 24^3 Kuhn cube minus centred PEC cube (81,648 tets), P2 / RK4, eps=4 sphere r=0.15, "
+            "impedance outer boundary, omega=4pi, seeded Gaussian source, CG rel. residual 1e-5")
+# CG iterations of this workload at CG_TOL, used only to extrapolate the oracle's
+# per-step time of the reference arm to a whole solve (the main arm uses the live count).
+CG_ITERS_FOR_REFERENCE = 35
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dg_stage_scatterer24_P2_fp32.md")
+STAGE_SRC = os.path.join(ROOT, "paper_2106_02858_gb300", "csrc", "dg_stage.cuh")
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------------------------
+# Oracle timing (CPU baseline / reference arm): runs in a child process, one thread.
+# ---------------------------------------------------------------------------------------------
+
+def _oracle_child(steps: int, warmup: int) -> None:
+    from paper_2106_02858_gb300 import inputs as I
+    from oracle.geometry import build_geometry
+    from oracle.timestep import Stepper, rk4_step
+    p = I.scatterer_sphere()
+    g = build_geometry(p.mesh.verts, p.mesh.tets, p.mesh.tags, p.eps, p.mu, p.order)
+    st = Stepper(g, p.omega)
+    import numpy as np
+    U = I.random_field(np.random.default_rng(0), p.nt, p.order)
+    phi = st.phi()  # source-free operator, as in the 2 n_iter + 1 source-free sweeps
+    times = []
+    for k in range(warmup + steps):
+        t0 = time.perf_counter()
+        U, _ = rk4_step(phi, k * st.dt, U, st.dt)
+        t1 = time.perf_counter()
+        if k >= warmup:
+            times.append(t1 - t0)
+    print(json.dumps({"step_s": times, "M": st.M, "ndof": p.ndof}))
+
+
+def oracle_sample(steps: int, warmup: int):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    cmd = [sys.executable, "-c", f"import bench; bench._oracle_child({steps}, {warmup})"]
+    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# ---------------------------------------------------------------------------------------------
+# Clock sampling during the timed region.
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv", "-lms", "200",
+                                          "-i", str(self.gpu), "-f", self.path],
+                                         stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for row in csv.reader(fh):
+                if not row or row[0].strip().startswith("index"):
+                    continue
+                rows.append([c.strip() for c in row])
+        os.unlink(self.path)
+        sm = [float(re.sub(r"[^0-9.]", "", r[1])) for r in rows if re.sub(r"[^0-9.]", "", r[1])]
+        smax = [float(re.sub(r"[^0-9.]", "", r[2])) for r in rows if re.sub(r"[^0-9.]", "", r[2])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------------------------
+# Roofline model of the stage kernel.
+# ---------------------------------------------------------------------------------------------
+
+def stage_algorithmic_bytes(nt: int, ndof: int, b: int) -> float:
+    """Algorithmic bytes of one source-free RK4 stage (nested form), averaged over a step.
+
+    Per step and dof: 11 field-vector accesses (stage 1 reads U, writes v; stages 2-4
+    read v and U and write v' or U); neighbour traces are re-reads of the same
+    vector, counted once.  Per tetrahedron and stage: 9 affine factors, 1/eps, 1/mu,
+    4 faces x (normal + 4 flux coefficients) in the sweep precision, and 4 int32
+    neighbour codes."""
+    field = 11.0 / 4.0 * b * ndof
+    geometry = (9 + 2 + 4 * 7) * b + 4 * 4
+    return field + geometry * nt
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the stage kernel from the committed ncu summary, if the
+    kernel source is unchanged since that capture; else None."""
+    if not os.path.exists(PROFILE_SUMMARY):
+        return None
+    txt = open(PROFILE_SUMMARY).read()
+    m_sha = re.search(r"stage kernel source sha256:\s*([0-9a-f]{64})", txt)
+    m_tr = re.search(r"dram bytes per launch \(read \+ write\):\s*([0-9.eE+]+)", txt)
+    if not (m_sha and m_tr):
+        return None
+    sha = hashlib.sha256(open(STAGE_SRC, "rb").read()).hexdigest()
+    return float(m_tr.group(1)) if sha == m_sha.group(1) else None
+
+
+# ---------------------------------------------------------------------------------------------
+# Arms.
+# ---------------------------------------------------------------------------------------------
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    r = oracle_sample(args.steps, args.warmup)
+    step_s = statistics.mean(r["step_s"])
+    steps_per_solve = r["M"] * (3 + 2 * CG_ITERS_FOR_REFERENCE)
+    value = 1.0 / (step_s * steps_per_solve)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "host CPU, one thread"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step = one RK4 step (4 operator applications) of the FP64 numpy oracle on "
+                                   f"the full 81,648-tet P2 mesh; solves/s extrapolated as 1 / (step time x M x "
+                                   f"(3 + 2 x {CG_ITERS_FOR_REFERENCE})) with M = {r['M']}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "dof_updates_per_s": r["ndof"] / step_s,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02858_gb300 import cmcg, inputs as I
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    prob = I.scatterer_sphere(seed=args.seed + rank)
+    h32, _m32 = cmcg.create_for_problem(prob, precision=cmcg.CMCG_FP32, device=local_rank)
+    stream = torch.cuda.current_stream(dev)
+    cmcg.cmcg_set_stream(h32, stream)
+    jr = torch.from_numpy(prob.j_re).to(dev)
+    ji = torch.from_numpy(prob.j_im).to(dev)
+    outs = [torch.empty(prob.nt, 3, prob.np_, dtype=torch.float64, device=dev) for _ in range(4)]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def solve():
+        return cmcg.cmcg_solve_device(h32, jr, ji, CG_TOL, MAX_ITER, *outs)
+
+    for _ in range(args.warmup):
+        info = solve()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    cmcg.cmcg_profile_enable(h32, True)
+    launches0 = cmcg.cmcg_kernel_launches(h32)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    infos = []
+    for k in range(args.steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        infos.append(solve())
+        evs[k][1].record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    launches = cmcg.cmcg_kernel_launches(h32) - launches0
+    free_ms, free_stages, src_ms, src_stages = cmcg.cmcg_profile_read(h32)
+    cmcg.cmcg_profile_enable(h32, False)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    total_s = sum(step_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([total_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    value = args.steps * world / total_s
+    iters = infos[-1].iters
+    periods = 3 + 2 * iters
+    dof_updates = prob.ndof * h32.steps * periods
+    e32 = [o.cpu().numpy() for o in outs]
+
+    # e2e: the host-buffer entry point, pinned inputs copied in and results read back every step.
+    pin = lambda a: torch.from_numpy(a).pin_memory().numpy()
+    jr_h, ji_h = pin(prob.j_re), pin(prob.j_im)
+    e2e_ms = []
+    for _ in range(max(1, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        cmcg.cmcg_solve(h32, jr_h, ji_h, CG_TOL, MAX_ITER)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    if world > 1:
+        t = torch.tensor([sum(e2e_ms) / 1e3], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    else:
+        e2e_total = sum(e2e_ms) / 1e3
+    nj = prob.nt * 3 * prob.np_ * 8
+    h2d, d2h = 2 * nj, 4 * nj
+
+    # FP64 plain solve of the same problem: accuracy of the FP32 result and the FP64 rate.
+    fp64 = None
+    if not args.skip_fp64:
+        h64, _m64 = cmcg.create_for_problem(prob, precision=cmcg.CMCG_FP64, device=local_rank)
+        cmcg.cmcg_set_stream(h64, stream)
+        outs64 = [torch.empty_like(o) for o in outs]
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        info64 = cmcg.cmcg_solve_device(h64, jr, ji, CG_TOL, MAX_ITER, *outs64)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e64 = [o.cpu().numpy() for o in outs64]
+        # (e, h) -> full (nt, 6, Np) real and imaginary parts
+        re32, im32 = np.concatenate([e32[0], e32[2]], axis=1), np.concatenate([e32[1], e32[3]], axis=1)
+        re64, im64 = np.concatenate([e64[0], e64[2]], axis=1), np.concatenate([e64[1], e64[3]], axis=1)
+        dr, di = re32 - re64, im32 - im64
+        num = cmcg.cmcg_inner(h64, dr, dr) + cmcg.cmcg_inner(h64, di, di)
+        den = cmcg.cmcg_inner(h64, re64, re64) + cmcg.cmcg_inner(h64, im64, im64)
+        fp64 = {"rel_l2": math.sqrt(num / den), "ms": a.elapsed_time(b), "iters": info64.iters}
+        h64.close()
+
+    # Roofline of the stage kernel over the timed region (source-free sweeps).
+    peak, peak_kind = peaks()
+    stage_us = free_ms * 1e3 / max(free_stages, 1)
+    alg = stage_algorithmic_bytes(prob.nt, prob.ndof, 4)
+    achieved = alg / (stage_us * 1e-6) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(), "kernel": "dg_stage_kernel<float> (P2, nested RK4 stage)",
+                "algorithmic_bytes_per_launch": alg, "avg_launch_us": stage_us, "peak_source": peak_kind}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        r = oracle_sample(2, 0)
+        step_s = statistics.mean(r["step_s"])
+        cpu_value = 1.0 / (step_s * h32.steps * periods)
+        cpu = {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"2 RK4 steps (8 operator applications) of the FP64 numpy oracle on the full mesh, "
+                         f"one thread; extrapolated to a solve as step time x {h32.steps} steps x {periods} "
+                         f"periods ({iters} CG iterations)",
+               "dof_updates_per_s": r["ndof"] / step_s}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "tets": prob.nt, "order": prob.order, "dofs": prob.ndof,
+                       "steps_per_period": h32.steps, "cg_tol": CG_TOL, "sweep_precision": "fp32",
+                       "cg_scalars": "fp64", "l2": "256 MiB buffer written between timed solves",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "cg_iters": iters, "periods_per_solve": periods,
+            "dof_updates_per_s": dof_updates * args.steps * world / total_s,
+            "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+            "rel_l2_vs_fp64": fp64["rel_l2"] if fp64 else None,
+            "fp64_plain_solves_per_s": 1e3 / fp64["ms"] if fp64 else None,
+            "fp64_plain_iters": fp64["iters"] if fp64 else None,
+            "e2e": {"value": args.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": roofline,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    h32.close()
+
+
+def profile_sweep(args):
+    """One source-free FP32 period sweep of the benchmark workload (968 stage launches);
+    the command profiled by ncu for the stage kernel."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02858_gb300 import cmcg, inputs as I
+    prob = I.scatterer_sphere(seed=args.seed)
+    h, _m = cmcg.create_for_problem(prob, precision=cmcg.CMCG_FP32)
+    dev = torch.device("cuda:0")
+    u0 = torch.from_numpy(I.random_field(np.random.default_rng(0), prob.nt, prob.order)).to(dev)
+    uT = torch.empty_like(u0)
+    cmcg.dgtd_period_forward_device(h, u0, None, None, uT)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_sweep": "done", "launches": cmcg.cmcg_kernel_launches(h)}))
+    h.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--profile-sweep", action="store_true", help="run one period sweep only (for ncu)")
+    args = ap.parse_args()
+    if args.profile_sweep:
+        profile_sweep(args)
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

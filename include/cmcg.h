@@ -193,6 +193,12 @@ int dgtd_period_adjoint_device(cmcg_handle* h, const double* wT, double* w0);
 int cmcg_solve(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
                double* e_im, double* h_re, double* h_im, cmcg_info* info);
 
+/* (u, v)_{eps,mu} = sum_K int_K eps E_u . E_v + mu H_u . H_v (Eq. innerproduct),
+ * i.e. V^T M U with the block-diagonal DG mass matrix, evaluated on the device
+ * in FP64 (the fields are first rounded to the handle's precision).  u, v:
+ * double[nt][6][Np] host arrays. */
+int cmcg_inner(cmcg_handle* h, const double* u, const double* v, double* out);
+
 /* Device-pointer form of cmcg_solve (same layout, double). */
 int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter,
                       double* e_re, double* e_im, double* h_re, double* h_im, cmcg_info* info);
@@ -200,6 +206,18 @@ int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, do
 /* Number of kernels the library launched on this handle since creation (a
  * counter kept on the host at every launch). */
 int64_t cmcg_kernel_launches(const cmcg_handle* h);
+
+/* Sweep timing.  cmcg_profile_enable(h, 1) resets the counters and makes
+ * every later period sweep record a CUDA event on the handle's stream before
+ * its first and after its last stage; 0 stops recording.  cmcg_profile_read
+ * waits for the recorded events and returns the summed sweep times and stage
+ * launch counts, separately for source-free sweeps (P_w, P*_w: nested RK form)
+ * and sweeps with the source or the filter (Algorithms rk2 / rk4 as printed).
+ * A sweep's time covers its stage kernels back to back, launch gaps included.
+ * Any output pointer may be NULL. */
+int cmcg_profile_enable(cmcg_handle* h, int on);
+int cmcg_profile_read(cmcg_handle* h, double* free_ms, int64_t* free_stages, double* source_ms,
+                      int64_t* source_stages);
 
 #ifdef __cplusplus
 }

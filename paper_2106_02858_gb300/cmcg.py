@@ -87,6 +87,10 @@ def _load() -> C.CDLL:
         "cmcg_solve_device": (C.c_int, [_vp, _vp, _vp, C.c_double, C.c_int, _vp, _vp, _vp, _vp,
                                         C.POINTER(cmcg_info)]),
         "cmcg_kernel_launches": (C.c_int64, [_vp]),
+        "cmcg_inner": (C.c_int, [_vp, _dp, _dp, C.POINTER(C.c_double)]),
+        "cmcg_profile_enable": (C.c_int, [_vp, C.c_int]),
+        "cmcg_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                        C.POINTER(C.c_int64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -99,7 +103,8 @@ _lib = _load()
 EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg_reference_matrices", "cmcg_create",
             "cmcg_destroy", "cmcg_set_stream", "cmcg_get_sizes", "dgtd_apply", "dgtd_period_forward",
             "dgtd_period_adjoint", "dgtd_period_forward_device", "dgtd_period_adjoint_device", "cmcg_solve",
-            "cmcg_solve_device", "cmcg_kernel_launches")
+            "cmcg_solve_device", "cmcg_kernel_launches", "cmcg_profile_enable", "cmcg_profile_read",
+            "cmcg_inner")
 
 
 def library_path() -> str:
@@ -247,6 +252,25 @@ def cmcg_get_sizes(h: Handle):
 
 def cmcg_kernel_launches(h: Handle) -> int:
     return int(_lib.cmcg_kernel_launches(h.ptr))
+
+
+def cmcg_inner(h: Handle, u, v) -> float:
+    """(u, v)_{eps,mu} on the device (FP64 accumulation)."""
+    u, v = _field(h, u, 6, "u"), _field(h, v, 6, "v")
+    out = C.c_double()
+    _check(_lib.cmcg_inner(h.ptr, _ptr(u), _ptr(v), C.byref(out)), "cmcg_inner")
+    return out.value
+
+
+def cmcg_profile_enable(h: Handle, on: bool = True) -> None:
+    _check(_lib.cmcg_profile_enable(h.ptr, int(bool(on))), "cmcg_profile_enable")
+
+
+def cmcg_profile_read(h: Handle):
+    """Returns (free_sweep_ms, free_stage_launches, source_sweep_ms, source_stage_launches)."""
+    fm, fs, sm, ss = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
+    _check(_lib.cmcg_profile_read(h.ptr, C.byref(fm), C.byref(fs), C.byref(sm), C.byref(ss)), "cmcg_profile_read")
+    return fm.value, fs.value, sm.value, ss.value
 
 
 def _field(h: Handle, u, ncomp=6, name="field"):

@@ -53,6 +53,17 @@ struct cmcg_handle {
   int64_t launches = 0;
   size_t bytes = 0;
   std::vector<std::complex<double>> fa, fb;  // filter weights per step 0..M
+  // sweep profiling
+  bool prof = false;
+  struct SweepEv {
+    cudaEvent_t a, b;
+    bool source;
+    int64_t stages;
+  };
+  std::vector<SweepEv> prof_ev;
+  size_t prof_used = 0;
+  double prof_ms[2] = {0, 0};
+  int64_t prof_stages[2] = {0, 0};
 };
 
 namespace {
@@ -150,9 +161,42 @@ StageArgs<R> blank() {
   return a;
 }
 
+// Sweep profiling: events around a sweep, collected lazily.
+cmcg_handle::SweepEv* prof_begin(cmcg_handle* h, bool source) {
+  if (!h->prof) return nullptr;
+  if (h->prof_used == h->prof_ev.size()) {
+    cmcg_handle::SweepEv e{};
+    if (cudaEventCreate(&e.a) != cudaSuccess || cudaEventCreate(&e.b) != cudaSuccess) return nullptr;
+    h->prof_ev.push_back(e);
+  }
+  cmcg_handle::SweepEv* e = &h->prof_ev[h->prof_used++];
+  e->source = source;
+  e->stages = h->launches;
+  cudaEventRecord(e->a, h->stream);
+  return e;
+}
+void prof_end(cmcg_handle* h, cmcg_handle::SweepEv* e) {
+  if (!e) return;
+  cudaEventRecord(e->b, h->stream);
+  e->stages = h->launches - e->stages;
+}
+// Folds recorded sweeps into the totals (waits for their events).
+void prof_collect(cmcg_handle* h) {
+  for (size_t i = 0; i < h->prof_used; ++i) {
+    cmcg_handle::SweepEv& e = h->prof_ev[i];
+    cudaEventSynchronize(e.b);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e.a, e.b);
+    h->prof_ms[e.source ? 1 : 0] += ms;
+    h->prof_stages[e.source ? 1 : 0] += e.stages;
+  }
+  h->prof_used = 0;
+}
+
 // Source-free sweep of Uw in place (nested RK form); adjoint flips the magnetic sign.
 template <typename R>
 void sweep_free(cmcg_handle* h, bool adjoint) {
+  cmcg_handle::SweepEv* pe = prof_begin(h, false);
   R* Uw = (R*)h->Uw;
   R* v[2] = {(R*)h->vA, (R*)h->vB};
   const int s = h->integrator;
@@ -171,11 +215,13 @@ void sweep_free(cmcg_handle* h, bool adjoint) {
       pp ^= 1;
     }
   }
+  prof_end(h, pe);
 }
 
 // Sweep with source (Algorithms rk2 / rk4 as printed) of Uw in place; optional on-the-fly filter.
 template <typename R>
 void sweep_source(cmcg_handle* h, bool with_source, bool filter) {
+  cmcg_handle::SweepEv* pe = prof_begin(h, true);
   R* Uw = (R*)h->Uw;
   R* vA = (R*)h->vA;
   R* vB = (R*)h->vB;
@@ -239,6 +285,7 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter) {
     filt(a, h->M);
     stage<R>(h, a);
   }
+  prof_end(h, pe);
 }
 
 template <typename R>
@@ -325,6 +372,19 @@ int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, con
   to_ext<R>(h, (const R*)h->vA, 6, 0, out, 6, 6);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
+  return CMCG_OK;
+}
+
+template <typename R>
+int inner_dev(cmcg_handle* h, const double* u, const double* v, double* out) {
+  to_int<R>(h, u, 6, (R*)h->Uw, 6, 0, 6, nullptr);
+  to_int<R>(h, v, 6, (R*)h->vA, 6, 0, 6, nullptr);
+  launch_dot<R>(h->q, (const R*)h->Uw, (const R*)h->vA, h->wdot, h->partials, h->nti, h->stream);
+  launch_finalize(h->partials, dot_blocks(h->nti), h->sc, 3, h->stream);
+  h->launches += 2;
+  CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *out = h->sc_host->rr_new;
   return CMCG_OK;
 }
 
@@ -424,6 +484,10 @@ void free_all(cmcg_handle* h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->sc_host) cudaFreeHost(h->sc_host);
+  for (auto& e : h->prof_ev) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
 }
 
 template <typename R>
@@ -627,6 +691,28 @@ int cmcg_get_sizes(const cmcg_handle* h, int64_t* nt, int* np, int* steps, doubl
 
 int64_t cmcg_kernel_launches(const cmcg_handle* h) { return h ? h->launches : 0; }
 
+int cmcg_profile_enable(cmcg_handle* h, int on) {
+  if (!h) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  prof_collect(h);
+  h->prof = on != 0;
+  h->prof_ms[0] = h->prof_ms[1] = 0;
+  h->prof_stages[0] = h->prof_stages[1] = 0;
+  return CMCG_OK;
+}
+
+int cmcg_profile_read(cmcg_handle* h, double* free_ms, int64_t* free_stages, double* source_ms,
+                      int64_t* source_stages) {
+  if (!h) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  prof_collect(h);
+  if (free_ms) *free_ms = h->prof_ms[0];
+  if (free_stages) *free_stages = h->prof_stages[0];
+  if (source_ms) *source_ms = h->prof_ms[1];
+  if (source_stages) *source_stages = h->prof_stages[1];
+  return CMCG_OK;
+}
+
 #define DISPATCH(h, call_f, call_d) ((h)->prec == CMCG_FP32 ? (call_f) : (call_d))
 
 int dgtd_apply(cmcg_handle* h, double t, const double* u, const double* j_re, const double* j_im, int adjoint,
@@ -701,6 +787,15 @@ int dgtd_period_adjoint(cmcg_handle* h, const double* wT, double* w0) {
   CK(cudaMemcpyAsync(w0, h->ext0, n * 8, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return CMCG_OK;
+}
+
+int cmcg_inner(cmcg_handle* h, const double* u, const double* v, double* out) {
+  if (!h || !u || !v || !out) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  const size_t n = size_t(h->nt) * 6 * h->np;
+  CK(cudaMemcpyAsync(h->ext0, u, n * 8, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->ext1, v, n * 8, cudaMemcpyHostToDevice, h->stream));
+  return DISPATCH(h, inner_dev<float>(h, h->ext0, h->ext1, out), inner_dev<double>(h, h->ext0, h->ext1, out));
 }
 
 int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,

@@ -7,9 +7,13 @@ Tolerances (relative, (eps, mu)-weighted L2 unless noted):
   polynomial).
 * FP32 operator: 1e-5 (single-rounding errors of ~6e-8 times the operator's
   cancellation); FP32 sweeps 1e-5 per period; FP32 filtered results 1e-4.
-* CMCG solves: with a fixed iteration count and no early stop the FP64 solve
-  follows the same CG recursion as the oracle: 1e-9.  Converged solves agree
-  within the CG tolerance times the conditioning of the filtered map: 1e-6.
+* CMCG solves.  CG on the normal operator (I - P*)(I - P) amplifies rounding
+  differently along the iteration: perturbing the oracle's own source by 1e-13
+  moves its filtered iterate by ~1e-13 after 2-4 iterations, by ~4e-6 after 8
+  (a transient where the residual grows), and by ~2e-12 once converged to
+  1e-8 (22 iterations on the 384-tet cube).  The checks therefore compare 4
+  fixed iterations at 1e-10 and the converged FP64 solve at 1e-9 (same
+  iteration count); the FP32 solve to 1e-5 is compared at 1e-4.
 
 Meshes span several 32-tet tiles with ragged tails (27 and 504 cubes per
 shape class), a distorted mesh with no repeated shapes (single sorted group),
@@ -136,12 +140,12 @@ def test_cmcg_fixed_iterations_match_oracle(lib):
     g = _geo(p)
     st = Stepper(g, p.omega)
     h, _ = lib.create_for_problem(p, precision=lib.CMCG_FP64)
-    e, hh, info = lib.cmcg_solve(h, p.j_re, p.j_im, tol=0.0, max_iter=8)
-    assert info.iters == 8 and info.periods == 19
-    ref = ocmcg.solve(st, p.j_re, p.j_im, tol=0.0, max_iter=8)
-    assert ref.iters == 8
+    e, hh, info = lib.cmcg_solve(h, p.j_re, p.j_im, tol=0.0, max_iter=4)
+    assert info.iters == 4 and info.periods == 11
+    ref = ocmcg.solve(st, p.j_re, p.j_im, tol=0.0, max_iter=4)
+    assert ref.iters == 4
     got = np.concatenate([e, hh], axis=1)
-    assert _rel(got, ref.filtered, g) < 1e-9
+    assert _rel(got, ref.filtered, g) < 1e-10
     assert abs(info.rel_residual - ref.residuals[-1]) < 1e-8 * ref.residuals[-1] + 1e-14
     h.close()
 
@@ -159,7 +163,7 @@ def test_cmcg_converged_solve_matches_oracle(lib, prec):
     e, hh, info = lib.cmcg_solve(h, p.j_re, p.j_im, tol=tol, max_iter=500)
     assert info.status == lib.CMCG_OK
     got = np.concatenate([e, hh], axis=1)
-    assert _rel(got, ref.filtered, g) < (1e-6 if prec == "fp64" else 1e-4)
+    assert _rel(got, ref.filtered, g) < (1e-9 if prec == "fp64" else 1e-4)
     if prec == "fp64":
         assert info.iters == ref.iters
     h.close()
