@@ -199,6 +199,31 @@ int cmcg_solve(cmcg_handle* h, const double* j_re, const double* j_im, double to
  * double[nt][6][Np] host arrays. */
 int cmcg_inner(cmcg_handle* h, const double* u, const double* v, double* out);
 
+/* Largest nt accepted by cmcg_inner_noalloc (128 tetrahedra per block x 8192 blocks). */
+#define CMCG_NOALLOC_MAX_TETS 1048576
+
+/* The paper has no counterpart: this is cmcg_inner without a handle and
+ * without any device allocation, for callers that cannot call cudaMalloc where
+ * they need the inner product (code whose device memory all belongs to its own
+ * pool allocator, stream-ordered pipelines that cudaMalloc / cudaFree would
+ * synchronise, callers that hold no handle because cmcg_create allocates).
+ * Computes (u, v)_{eps,mu} = sum_K w_K0 E_u.Mref E_v + w_K1 H_u.Mref H_v with the
+ * unit-tetrahedron mass matrix Mref of order q, accumulated in FP64.
+ *   order: q in 1..3;  nt: 1..CMCG_NOALLOC_MAX_TETS (larger: CMCG_ERR_INVALID_ARG,
+ *   nothing launched);  u, v: device double[nt][6][Np] in the boundary layout;
+ *   w: device double[nt][2] = (eps_K, mu_K) times |det(v1-v0, v2-v0, v3-v0)|
+ *   (six times the volume of K);  out: device double[1].
+ * Runs on `stream` (a cudaStream_t, NULL = legacy default stream) of the
+ * current device and returns once its two kernels are launched; *out is valid
+ * when the stream reaches that point.  It reduces through a 64 KiB static
+ * device array that every GPU loading the library holds until the process
+ * exits.  The first call on a device does a one-time set-up (uploads the mass
+ * matrices, looks up the array's device address); make that first call before
+ * any stream capture.  All calls share the array: calls that overlap on the
+ * GPU race. */
+int cmcg_inner_noalloc(int order, int64_t nt, const double* u, const double* v, const double* w, double* out,
+                       void* stream);
+
 /* Device-pointer form of cmcg_solve (same layout, double). */
 int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter,
                       double* e_re, double* e_im, double* h_re, double* h_im, cmcg_info* info);

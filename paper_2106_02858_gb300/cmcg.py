@@ -88,6 +88,7 @@ def _load() -> C.CDLL:
                                         C.POINTER(cmcg_info)]),
         "cmcg_kernel_launches": (C.c_int64, [_vp]),
         "cmcg_inner": (C.c_int, [_vp, _dp, _dp, C.POINTER(C.c_double)]),
+        "cmcg_inner_noalloc": (C.c_int, [C.c_int, C.c_int64, _vp, _vp, _vp, _vp, _vp]),
         "cmcg_profile_enable": (C.c_int, [_vp, C.c_int]),
         "cmcg_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                         C.POINTER(C.c_int64)]),
@@ -104,7 +105,8 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_destroy", "cmcg_set_stream", "cmcg_get_sizes", "dgtd_apply", "dgtd_period_forward",
             "dgtd_period_adjoint", "dgtd_period_forward_device", "dgtd_period_adjoint_device", "cmcg_solve",
             "cmcg_solve_device", "cmcg_kernel_launches", "cmcg_profile_enable", "cmcg_profile_read",
-            "cmcg_inner")
+            "cmcg_inner", "cmcg_inner_noalloc")
+CMCG_NOALLOC_MAX_TETS = 1048576
 
 
 def library_path() -> str:
@@ -260,6 +262,23 @@ def cmcg_inner(h: Handle, u, v) -> float:
     out = C.c_double()
     _check(_lib.cmcg_inner(h.ptr, _ptr(u), _ptr(v), C.byref(out)), "cmcg_inner")
     return out.value
+
+
+def cmcg_inner_noalloc(order: int, nt: int, u, v, w, out, stream=None) -> None:
+    """Allocation-free (u, v)_{eps,mu} for callers that cannot call cudaMalloc.
+
+    u, v: float64 CUDA tensors (nt, 6, Np); w: (nt, 2) = (eps, mu) times
+    |det(v1-v0, v2-v0, v3-v0)| per tetrahedron; out: a 1-element float64 CUDA
+    tensor, written asynchronously on ``stream`` (torch stream, raw handle or
+    None).  The first call on a device does a one-time set-up, so make it before
+    any stream capture; overlapping calls race on the shared static scratch."""
+    raw = getattr(stream, "cuda_stream", stream)
+    rc = _lib.cmcg_inner_noalloc(int(order), int(nt), _dev(u), _dev(v), _dev(w), _dev(out),
+                                 C.c_void_p(raw) if raw else None)
+    if rc == CMCG_ERR_INVALID_ARG and nt > CMCG_NOALLOC_MAX_TETS:
+        raise CMCGError(rc, f"cmcg_inner_noalloc: nt = {nt} exceeds the static scratch limit of "
+                            f"{CMCG_NOALLOC_MAX_TETS} tetrahedra")
+    _check(rc, "cmcg_inner_noalloc")
 
 
 def cmcg_profile_enable(h: Handle, on: bool = True) -> None:
