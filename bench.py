@@ -349,13 +349,14 @@ def profile_sweep(args):
     __graft_entry__.build()
     from paper_2106_02858_gb300 import cmcg, inputs as I
     prob = I.scatterer_sphere(seed=args.seed)
-    h, _m = cmcg.create_for_problem(prob, precision=cmcg.CMCG_FP32)
+    h, _m = cmcg.create_for_problem(prob, precision=cmcg.CMCG_FP32, stage_variant=args.stage_variant)
     dev = torch.device("cuda:0")
     u0 = torch.from_numpy(I.random_field(np.random.default_rng(0), prob.nt, prob.order)).to(dev)
     uT = torch.empty_like(u0)
     cmcg.dgtd_period_forward_device(h, u0, None, None, uT)
     torch.cuda.synchronize()
-    print(json.dumps({"profile_sweep": "done", "launches": cmcg.cmcg_kernel_launches(h)}))
+    print(json.dumps({"profile_sweep": "done", "launches": cmcg.cmcg_kernel_launches(h),
+                      "tuning": cmcg.cmcg_get_tuning(h)}))
     h.close()
 
 
@@ -369,6 +370,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--profile-sweep", action="store_true", help="run one period sweep only (for ncu)")
+    ap.add_argument("--stage-variant", type=int, default=0, help="force a stage-kernel form (see cmcg_options)")
     args = ap.parse_args()
     if args.profile_sweep:
         profile_sweep(args)

@@ -100,7 +100,14 @@ typedef struct cmcg_mesh {
  *   hbm_budget_bytes: > 0 makes cmcg_create fail with
  *                     CMCG_ERR_OUT_OF_MEMORY if the handle would need more
  *                     device memory than this.
- *   device:           CUDA device ordinal. */
+ *   device:           CUDA device ordinal.
+ *   stage_variant:    0 = time the stage-kernel forms on this mesh at
+ *                     creation and keep the fastest; k > 0 forces form k - 1:
+ *                     0..2 = scalar kernel (two threads per tetrahedron) with
+ *                     at least 1, 3, 4 resident 128-thread blocks per SM
+ *                     (FP64: 0 only); 3 (FP32) = packed kernel, two
+ *                     tetrahedra per lane with f32x2 FMAs.  Results do not
+ *                     depend on it beyond rounding. */
 typedef struct cmcg_options {
   int order;
   int precision;
@@ -109,7 +116,8 @@ typedef struct cmcg_options {
   double c_q;
   int64_t hbm_budget_bytes;
   int device;
-  int reserved[7];
+  int stage_variant;
+  int reserved[6];
 } cmcg_options;
 
 /* Per-solve report. */
@@ -159,6 +167,12 @@ void cmcg_destroy(cmcg_handle* h);
 /* Uses the given cudaStream_t (as void*) for all later work of the handle;
  * NULL selects the legacy default stream. */
 int cmcg_set_stream(cmcg_handle* h, void* stream);
+
+/* Stage-kernel form in use (0-based, as stage_variant - 1) and, when it was
+ * chosen by timing at creation, the measured microseconds per stage of each
+ * form (8 entries: [0..2] scalar variants, [3] packed kernel; -1 where not
+ * timed).  Any pointer may be NULL. */
+int cmcg_get_tuning(const cmcg_handle* h, int* variant, double* us_per_stage);
 
 /* Sizes of the handle: nt, Np, M (steps per period), dt, number of doubles of
  * one full field (6 Np nt).  Any pointer may be NULL. */

@@ -42,7 +42,7 @@ class cmcg_mesh(C.Structure):
 class cmcg_options(C.Structure):
     _fields_ = [("order", C.c_int), ("precision", C.c_int), ("flux", C.c_int), ("steps_per_period", C.c_int),
                 ("c_q", C.c_double), ("hbm_budget_bytes", C.c_int64), ("device", C.c_int),
-                ("reserved", C.c_int * 7)]
+                ("stage_variant", C.c_int), ("reserved", C.c_int * 6)]
 
 
 class cmcg_info(C.Structure):
@@ -76,6 +76,7 @@ def _load() -> C.CDLL:
                                   C.POINTER(_vp)]),
         "cmcg_destroy": (None, [_vp]),
         "cmcg_set_stream": (C.c_int, [_vp, _vp]),
+        "cmcg_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "cmcg_get_sizes": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                      C.POINTER(C.c_double), C.POINTER(C.c_int64)]),
         "dgtd_apply": (C.c_int, [_vp, C.c_double, _dp, _dp, _dp, C.c_int, _dp]),
@@ -105,7 +106,7 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_destroy", "cmcg_set_stream", "cmcg_get_sizes", "dgtd_apply", "dgtd_period_forward",
             "dgtd_period_adjoint", "dgtd_period_forward_device", "dgtd_period_adjoint_device", "cmcg_solve",
             "cmcg_solve_device", "cmcg_kernel_launches", "cmcg_profile_enable", "cmcg_profile_read",
-            "cmcg_inner", "cmcg_inner_noalloc")
+            "cmcg_inner", "cmcg_inner_noalloc", "cmcg_get_tuning")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
 
@@ -147,11 +148,11 @@ def _check(rc: int, where: str, allow_not_converged: bool = False) -> int:
 
 def cmcg_default_options(order: int = 1, precision: int = CMCG_FP64, flux: int = CMCG_FLUX_UPWIND,
                          steps_per_period: int = 0, c_q: float = 0.0, hbm_budget_bytes: int = 0,
-                         device: int = 0) -> cmcg_options:
+                         device: int = 0, stage_variant: int = 0) -> cmcg_options:
     o = cmcg_options()
     _lib.cmcg_default_options(C.byref(o))
     o.order, o.precision, o.flux, o.steps_per_period = order, precision, flux, steps_per_period
-    o.c_q, o.hbm_budget_bytes, o.device = c_q, hbm_budget_bytes, device
+    o.c_q, o.hbm_budget_bytes, o.device, o.stage_variant = c_q, hbm_budget_bytes, device, stage_variant
     return o
 
 
@@ -250,6 +251,14 @@ def cmcg_get_sizes(h: Handle):
     _check(_lib.cmcg_get_sizes(h.ptr, C.byref(nt), C.byref(np_), C.byref(steps), C.byref(dt), C.byref(fl)),
            "cmcg_get_sizes")
     return nt.value, np_.value, steps.value, dt.value, fl.value
+
+
+def cmcg_get_tuning(h: Handle):
+    """(variant in use, microseconds per stage of each timed variant or None)."""
+    v = C.c_int()
+    us = (C.c_double * 8)()
+    _check(_lib.cmcg_get_tuning(h.ptr, C.byref(v), us), "cmcg_get_tuning")
+    return v.value, [x if x >= 0 else None for x in us]
 
 
 def cmcg_kernel_launches(h: Handle) -> int:
@@ -352,9 +361,10 @@ def cmcg_solve_device(h: Handle, j_re, j_im, tol: float, max_iter: int, e_re, e_
 
 
 def create_for_problem(problem, precision: int = CMCG_FP64, flux: int = CMCG_FLUX_UPWIND, steps_per_period: int = 0,
-                       device: int = 0, hbm_budget_bytes: int = 0):
+                       device: int = 0, hbm_budget_bytes: int = 0, stage_variant: int = 0):
     """Convenience: cmcg_create from an ``inputs.Problem``; returns (handle, mesh arrays)."""
     mesh = make_mesh(problem.mesh.verts, problem.mesh.tets, problem.mesh.tags)
     opt = cmcg_default_options(order=problem.order, precision=precision, flux=flux,
-                               steps_per_period=steps_per_period, device=device, hbm_budget_bytes=hbm_budget_bytes)
+                               steps_per_period=steps_per_period, device=device, hbm_budget_bytes=hbm_budget_bytes,
+                               stage_variant=stage_variant)
     return cmcg_create(mesh, problem.eps, problem.mu, problem.omega, opt), mesh

@@ -52,6 +52,10 @@ struct cmcg_handle {
   double *ext0 = nullptr, *ext1 = nullptr, *ext2 = nullptr, *ext3 = nullptr;
   int64_t launches = 0;
   size_t bytes = 0;
+  int variant = 0;     // occupancy variant of the per-stage kernel
+  int packed_minb = 0; // > 0 (FP32): every stage runs on the packed two-tetrahedra-per-lane kernel
+  int nsm = 0;
+  double tune_us[8];
   std::vector<std::complex<double>> fa, fb;  // filter weights per step 0..M
   // sweep profiling
   bool prof = false;
@@ -147,9 +151,18 @@ void stage(cmcg_handle* h, StageArgs<R>& a) {
   a.gface = (const R*)h->gface;
   a.nbr = h->nbr;
   a.nti = h->nti;
-  if (h->q == 1) launch_stage<1, R>(a, h->stream);
-  else if (h->q == 2) launch_stage<2, R>(a, h->stream);
-  else launch_stage<3, R>(a, h->stream);
+  if constexpr (sizeof(R) == 4) {
+    if (h->packed_minb > 0) {
+      if (h->q == 1) launch_stage_packed<1>(a, h->stream, h->packed_minb);
+      else if (h->q == 2) launch_stage_packed<2>(a, h->stream, h->packed_minb);
+      else launch_stage_packed<3>(a, h->stream, h->packed_minb);
+      h->launches++;
+      return;
+    }
+  }
+  if (h->q == 1) launch_stage<1, R>(a, h->stream, h->variant);
+  else if (h->q == 2) launch_stage<2, R>(a, h->stream, h->variant);
+  else launch_stage<3, R>(a, h->stream, h->variant);
   h->launches++;
 }
 
@@ -286,6 +299,76 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter) {
     stage<R>(h, a);
   }
   prof_end(h, pe);
+}
+
+// Times the stage-kernel forms on this mesh with a nested source-free stage on
+// zero fields (3 warm-up + 12 timed launches each): the scalar kernel at each
+// occupancy variant and, in FP32, the packed kernel; keeps the fastest.
+// tune_us[0..2]: scalar variants, tune_us[3]: packed.
+template <typename R>
+int autotune(cmcg_handle* h, int nvariants) {
+  for (double& x : h->tune_us) x = -1;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaMemsetAsync(h->Uw, 0, h->nvec * h->rsize, h->stream));
+  const int64_t launches0 = h->launches;
+  auto time_one = [&](double* us) -> int {
+    auto run = [&](int n) {
+      for (int k = 0; k < n; ++k) {
+        StageArgs<R> a = blank<R>();
+        a.vin = (const R*)h->Uw;
+        a.base = (const R*)h->vB;
+        a.out = (R*)h->vA;
+        a.c_out = R(h->dt);
+        stage<R>(h, a);
+      }
+    };
+    run(1);
+    if (cudaGetLastError() != cudaSuccess) {  // launch rejected (configuration): form unavailable
+      *us = -1;
+      return CMCG_OK;
+    }
+    run(2);
+    CK(cudaEventRecord(e0, h->stream));
+    run(12);
+    CK(cudaEventRecord(e1, h->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaGetLastError());
+    float ms = 0;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    *us = 1e3 * ms / 12;
+    return CMCG_OK;
+  };
+  CK(cudaMemsetAsync(h->vB, 0, h->nvec * h->rsize, h->stream));
+  double best = 1e300;
+  int bestv = 0;
+  h->packed_minb = 0;
+  for (int v = 0; v < nvariants; ++v) {
+    h->variant = v;
+    double us;
+    int rc = time_one(&us);
+    if (rc) return rc;
+    h->tune_us[v] = us;
+    if (us >= 0 && us < best) {
+      best = us;
+      bestv = v;
+    }
+  }
+  h->variant = bestv;
+  if (sizeof(R) == 4) {
+    h->packed_minb = 2;
+    double us;
+    int rc = time_one(&us);
+    if (rc) return rc;
+    h->tune_us[3] = us;
+    if (!(us >= 0 && us < best)) h->packed_minb = 0;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->launches = launches0;
+  CK(cudaGetLastError());
+  return CMCG_OK;
 }
 
 template <typename R>
@@ -661,6 +744,26 @@ int cmcg_create(const cmcg_mesh* mesh, const double* eps, const double* mu, doub
   if (e == cudaSuccess) e = cudaMemcpy(h->inv_eps, inv_eps.data(), L.nt * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(h->ACC, 0, vb);
   if (e != cudaSuccess) return fail(cuda_fail(e));
+  {
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, opt.device) != cudaSuccess) return fail(CMCG_ERR_CUDA);
+    h->nsm = nsm;
+  }
+  for (double& x : h->tune_us) x = -1;
+  if (opt.stage_variant > 0) {
+    const int nv = h->prec == CMCG_FP32 ? STAGE_VARIANTS_F32 : 1;
+    const int k = opt.stage_variant - 1;
+    if (k < nv) {
+      h->variant = k;
+    } else if (k == 3 && h->prec == CMCG_FP32) {
+      h->packed_minb = 2;
+    } else {
+      return fail(CMCG_ERR_INVALID_ARG);
+    }
+  } else {
+    rc = h->prec == CMCG_FP32 ? autotune<float>(h, STAGE_VARIANTS_F32) : autotune<double>(h, 1);
+    if (rc) return fail(rc);
+  }
   h->launches = 0;
   *out = h;
   return CMCG_OK;
@@ -690,6 +793,14 @@ int cmcg_get_sizes(const cmcg_handle* h, int64_t* nt, int* np, int* steps, doubl
 }
 
 int64_t cmcg_kernel_launches(const cmcg_handle* h) { return h ? h->launches : 0; }
+
+int cmcg_get_tuning(const cmcg_handle* h, int* variant, double* us_per_stage) {
+  if (!h) return CMCG_ERR_INVALID_ARG;
+  if (variant) *variant = h->packed_minb > 0 ? 3 : h->variant;
+  if (us_per_stage)
+    for (int i = 0; i < 8; ++i) us_per_stage[i] = h->tune_us[i];
+  return CMCG_OK;
+}
 
 int cmcg_profile_enable(cmcg_handle* h, int on) {
   if (!h) return CMCG_ERR_INVALID_ARG;

@@ -80,7 +80,7 @@ struct HostLayout {
   int ngroups = 0;
 };
 constexpr int GV = 12;  // G (9, d r_b / d x_a at [b*3+a]), 1/eps, 1/mu, pad
-constexpr int GF = 8;   // nx, ny, nz, aE, bE, aH, bH, pad
+constexpr int GF = 8;   // nx, ny, nz, bH, aH, -bE, aE, pad  (see setup.cpp)
 
 int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
                         const cmcg_options* opt, HostLayout* out, bool build_layout, std::string* why);
@@ -117,10 +117,16 @@ struct StageArgs {
 };
 
 // Kernel launchers, one translation unit per order.
+// variant: occupancy variant of the stage kernel (FP32: 0..2 = at least 1, 3, 4
+// resident 128-thread blocks per SM; FP64 has one variant).
+constexpr int STAGE_VARIANTS_F32 = 3;
 template <int Q, typename R>
-void launch_stage(const StageArgs<R>& a, cudaStream_t s);
+void launch_stage(const StageArgs<R>& a, cudaStream_t s, int variant);
 template <int Q>
 void upload_constants(const RefMats& rm);
+// Packed FP32 stage kernel (two tetrahedra per lane, f32x2 FMA, at least 2 resident blocks).
+template <int Q>
+void launch_stage_packed(const StageArgs<float>& a, cudaStream_t s, int minb);
 
 // Vector kernels (vec.cu).
 struct Scalars {

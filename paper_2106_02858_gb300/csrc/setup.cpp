@@ -284,11 +284,15 @@ int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* 
         code = mesh->face_tags[4 * e + f] == CMCG_TAG_PEC ? NBR_PEC : NBR_IMP;
       }
       out->nbr[(tile * 4 + f) * TILE + lane] = code;
+      // E-rows flux  fE = aE (dE - n (n.dE)) - bE n x dH,  H-rows flux  fH = bH n x dE + aH (dH - n (n.dH))
+      // with aE = fscale / (eps (Z- + Z+)), bE = Z+ aE, aH = fscale / (mu (Y- + Y+)), bH = Y+ aH.
+      // Stored per half of the thread pair: (k1, k2) = (bH, aH) for the thread that owns E and
+      // computes Phi_H, (-bE, aE) for the thread that owns H and computes Phi_E.
       const double aE = fscale / eps[e] / (Zm + Zp), aH = fscale / mu[e] / (Ym + Yp);
-      gf(3) = centred ? 0.0 : aE;
-      gf(4) = Zp * aE;
-      gf(5) = centred ? 0.0 : aH;
-      gf(6) = Yp * aH;
+      gf(3) = Yp * aH;
+      gf(4) = centred ? 0.0 : aH;
+      gf(5) = -Zp * aE;
+      gf(6) = centred ? 0.0 : aE;
     }
   }
   out->ext_of_int = std::move(ext_of_int);

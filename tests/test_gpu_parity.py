@@ -209,3 +209,32 @@ def test_hbm_budget_is_enforced(lib):
     with pytest.raises(lib.CMCGError) as ei:
         lib.create_for_problem(p, hbm_budget_bytes=1000)
     assert ei.value.code == lib.CMCG_ERR_OUT_OF_MEMORY
+
+
+@pytest.mark.parametrize("q", [1, 2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_every_stage_kernel_form_matches_oracle(lib, q, prec):
+    """Each forced stage-kernel form (scalar occupancy variants, packed FP32 kernel) gives the
+    oracle's sweeps: the autotuner's choice cannot change results."""
+    from oracle.timestep import Stepper
+    p = _problem("scatterer8", q) if q < 3 else _problem("cube3", q)
+    g = _geo(p)
+    st = Stepper(g, p.omega)
+    rng = np.random.default_rng(17)
+    U = I.random_field(rng, p.nt, q)
+    refF, refA = st.P(U), st.P_star(U)
+    tol = 1e-12 if prec == "fp64" else 1e-5
+    forms = [1, 2, 3, 4, 5] if prec == "fp32" else [1, 2, 4]
+    tried = 0
+    for k in forms:
+        try:
+            h, _ = lib.create_for_problem(p, precision=lib.CMCG_FP64 if prec == "fp64" else lib.CMCG_FP32,
+                                          stage_variant=k)
+        except lib.CMCGError as e:
+            assert e.code == lib.CMCG_ERR_INVALID_ARG  # form does not fit this order / precision
+            continue
+        tried += 1
+        assert _rel(lib.dgtd_period_forward(h, U), refF, g) < tol, k
+        assert _rel(lib.dgtd_period_adjoint(h, U), refA, g) < tol, k
+        h.close()
+    assert tried == (4 if prec == "fp32" else 1)
