@@ -161,6 +161,29 @@ int cmcg_reference_matrices(int order, double* mass, double* dr, double* ds, dou
 int cmcg_create(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
                 const cmcg_options* opt, cmcg_handle** out);
 
+/* One problem of a batch: a mesh, its element permittivity / permeability and
+ * its angular frequency. */
+typedef struct cmcg_problem {
+  const cmcg_mesh* mesh;
+  const double* eps;
+  const double* mu;
+  double omega;
+} cmcg_problem;
+
+/* Builds a handle over a batch of nprob independent problems sharing the
+ * options (order, precision, flux, device ...); meshes, materials, frequencies
+ * and steps per period may differ (many sources on one mesh: pass the same
+ * mesh nprob times).  Every stage launch covers all problems; each problem
+ * keeps its own CG state and stops when it converges.  The single-problem
+ * entry points (dgtd_*, cmcg_inner, cmcg_solve[_device]) need nprob == 1. */
+int cmcg_create_batch(int nprob, const cmcg_problem* probs, const cmcg_options* opt, cmcg_handle** out);
+
+/* Number of problems of a handle (0 for NULL). */
+int cmcg_batch_size(const cmcg_handle* h);
+
+/* nt, steps per period and dt of problem p.  Any output pointer may be NULL. */
+int cmcg_get_problem(const cmcg_handle* h, int p, int64_t* nt, int* steps, double* dt);
+
 /* Releases the device state.  NULL is ignored. */
 void cmcg_destroy(cmcg_handle* h);
 
@@ -237,6 +260,21 @@ int cmcg_inner(cmcg_handle* h, const double* u, const double* v, double* out);
  * GPU race. */
 int cmcg_inner_noalloc(int order, int64_t nt, const double* u, const double* v, const double* w, double* out,
                        void* stream);
+
+/* CMCG for every problem of a batch handle (Algorithm cmcg per problem; all
+ * problems sweep together, converged ones stop updating).  Arrays of nprob
+ * host pointers: j_re[p], j_im[p] (j_im or any j_im[p] may be NULL) are
+ * double[nt_p][3][Np]; e_re[p], e_im[p], h_re[p], h_im[p] likewise.  info (may
+ * be NULL) receives nprob reports.  Returns the most severe status over the
+ * problems (an error, else CMCG_NOT_CONVERGED if any problem reached max_iter). */
+int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol, int max_iter,
+                     double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im,
+                     cmcg_info* info);
+
+/* Device-pointer form of cmcg_solve_batch (the pointer arrays live on the host). */
+int cmcg_solve_batch_device(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol,
+                            int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
+                            double* const* h_im, cmcg_info* info);
 
 /* Device-pointer form of cmcg_solve (same layout, double). */
 int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter,

@@ -51,6 +51,11 @@ class cmcg_info(C.Structure):
                 ("reserved", C.c_double * 5)]
 
 
+class cmcg_problem(C.Structure):
+    _fields_ = [("mesh", C.POINTER(cmcg_mesh)), ("eps", C.POINTER(C.c_double)), ("mu", C.POINTER(C.c_double)),
+                ("omega", C.c_double)]
+
+
 class CMCGError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {cmcg_status_string(code)} ({code})")
@@ -74,6 +79,14 @@ def _load() -> C.CDLL:
         "cmcg_reference_matrices": (C.c_int, [C.c_int, _dp, _dp, _dp, _dp, _dp]),
         "cmcg_create": (C.c_int, [C.POINTER(cmcg_mesh), _dp, _dp, C.c_double, C.POINTER(cmcg_options),
                                   C.POINTER(_vp)]),
+        "cmcg_create_batch": (C.c_int, [C.c_int, C.POINTER(cmcg_problem), C.POINTER(cmcg_options), C.POINTER(_vp)]),
+        "cmcg_batch_size": (C.c_int, [_vp]),
+        "cmcg_get_problem": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "cmcg_solve_batch": (C.c_int, [_vp, C.POINTER(_dp), C.POINTER(_dp), C.c_double, C.c_int, C.POINTER(_dp),
+                                       C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp), C.POINTER(cmcg_info)]),
+        "cmcg_solve_batch_device": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.c_double, C.c_int,
+                                              C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
+                                              C.POINTER(cmcg_info)]),
         "cmcg_destroy": (None, [_vp]),
         "cmcg_set_stream": (C.c_int, [_vp, _vp]),
         "cmcg_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -106,7 +119,8 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_destroy", "cmcg_set_stream", "cmcg_get_sizes", "dgtd_apply", "dgtd_period_forward",
             "dgtd_period_adjoint", "dgtd_period_forward_device", "dgtd_period_adjoint_device", "cmcg_solve",
             "cmcg_solve_device", "cmcg_kernel_launches", "cmcg_profile_enable", "cmcg_profile_read",
-            "cmcg_inner", "cmcg_inner_noalloc", "cmcg_get_tuning")
+            "cmcg_inner", "cmcg_inner_noalloc", "cmcg_get_tuning", "cmcg_create_batch", "cmcg_batch_size",
+            "cmcg_get_problem", "cmcg_solve_batch", "cmcg_solve_batch_device")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
 
@@ -201,11 +215,12 @@ def cmcg_reference_matrices(order: int):
 
 
 class Handle:
-    """Owns a cmcg_handle (cmcg_create / cmcg_destroy)."""
+    """Owns a cmcg_handle (cmcg_create / cmcg_create_batch / cmcg_destroy)."""
 
-    def __init__(self, ptr: int, nt: int, np_: int, steps: int, dt: float):
+    def __init__(self, ptr: int, nt: int, np_: int, steps: int, dt: float, problems=None):
         self.ptr = C.c_void_p(ptr)
         self.nt, self.np, self.steps, self.dt = nt, np_, steps, dt
+        self.problems = problems or [(nt, steps, dt)]  # (nt, steps, dt) per problem
 
     def close(self):
         if self.ptr is not None and self.ptr.value:
@@ -234,6 +249,65 @@ def cmcg_create(mesh: MeshArrays, eps, mu, omega: float, opt: cmcg_options) -> H
     _check(_lib.cmcg_get_sizes(out, C.byref(nt), C.byref(np_), C.byref(steps), C.byref(dt), C.byref(fl)),
            "cmcg_get_sizes")
     return Handle(out.value, nt.value, np_.value, steps.value, dt.value)
+
+
+def cmcg_create_batch(problems, opt: cmcg_options) -> Handle:
+    """``problems``: list of (MeshArrays, eps, mu, omega)."""
+    keep = []
+    arr = (cmcg_problem * len(problems))()
+    for i, (mesh, eps, mu, omega) in enumerate(problems):
+        e, m = _f64(eps), _f64(mu)
+        keep += [mesh, e, m]
+        arr[i] = cmcg_problem(C.pointer(mesh.struct), _ptr(e), _ptr(m), float(omega))
+    out = C.c_void_p()
+    _check(_lib.cmcg_create_batch(len(problems), arr, C.byref(opt), C.byref(out)), "cmcg_create_batch")
+    n = _lib.cmcg_batch_size(out)
+    probs = []
+    for p in range(n):
+        nt, steps, dt = C.c_int64(), C.c_int(), C.c_double()
+        _check(_lib.cmcg_get_problem(out, p, C.byref(nt), C.byref(steps), C.byref(dt)), "cmcg_get_problem")
+        probs.append((nt.value, steps.value, dt.value))
+    np_ = (opt.order + 1) * (opt.order + 2) * (opt.order + 3) // 6
+    return Handle(out.value, probs[0][0], np_, probs[0][1], probs[0][2], problems=probs)
+
+
+def cmcg_batch_size(h: Handle) -> int:
+    return int(_lib.cmcg_batch_size(h.ptr))
+
+
+def cmcg_get_problem(h: Handle, p: int):
+    nt, steps, dt = C.c_int64(), C.c_int(), C.c_double()
+    _check(_lib.cmcg_get_problem(h.ptr, p, C.byref(nt), C.byref(steps), C.byref(dt)), "cmcg_get_problem")
+    return nt.value, steps.value, dt.value
+
+
+def cmcg_solve_batch(h: Handle, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 1000):
+    """j_re, j_im: lists of (nt_p, 3, Np) arrays.  Returns (list of e, list of h, list of cmcg_info)."""
+    n = len(h.problems)
+    jr = [_f64(j_re[p], (h.problems[p][0], 3, h.np), "j_re") for p in range(n)]
+    ji = [None if (j_im is None or j_im[p] is None) else _f64(j_im[p], (h.problems[p][0], 3, h.np), "j_im")
+          for p in range(n)]
+    outs = [[np.empty((h.problems[p][0], 3, h.np)) for p in range(n)] for _ in range(4)]
+    P = C.POINTER(C.c_double)
+    arr = lambda xs: (P * n)(*[_ptr(x) if x is not None else P() for x in xs])
+    infos = (cmcg_info * n)()
+    rc = _lib.cmcg_solve_batch(h.ptr, arr(jr), arr(ji), float(tol), int(max_iter), arr(outs[0]), arr(outs[1]),
+                               arr(outs[2]), arr(outs[3]), infos)
+    _check(rc, "cmcg_solve_batch", allow_not_converged=True)
+    e = [outs[0][p] + 1j * outs[1][p] for p in range(n)]
+    hh = [outs[2][p] + 1j * outs[3][p] for p in range(n)]
+    return e, hh, list(infos)
+
+
+def cmcg_solve_batch_device(h: Handle, j_re, j_im, tol: float, max_iter: int, e_re, e_im, h_re, h_im):
+    """Lists (one per problem) of contiguous float64 CUDA tensors; j_im entries may be None."""
+    n = len(h.problems)
+    arr = lambda xs: (C.c_void_p * n)(*[_dev(x) if x is not None else C.c_void_p() for x in xs])
+    infos = (cmcg_info * n)()
+    rc = _lib.cmcg_solve_batch_device(h.ptr, arr(j_re), arr(j_im if j_im is not None else [None] * n), float(tol),
+                                      int(max_iter), arr(e_re), arr(e_im), arr(h_re), arr(h_im), infos)
+    _check(rc, "cmcg_solve_batch_device", allow_not_converged=True)
+    return list(infos)
 
 
 def cmcg_destroy(h: Handle) -> None:

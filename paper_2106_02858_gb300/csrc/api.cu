@@ -1,23 +1,30 @@
 // C ABI of libcmcg: handle life cycle, period sweeps and the CMCG driver.
 //
-// Sweeps (Section 4.1.2, Algorithms rk2 / rk4).  Every stage is one launch of
-// the stage kernel over all tetrahedra; the state being propagated lives in
-// the handle's work vector Uw.
-//   * source-free sweeps (P_w, P*_w) use the nested (Horner) form of the RK
-//     polynomial, v <- U + (dt / k) B v for k = s, ..., 1, which is the same
-//     polynomial sum_k (dt B)^k / k! as Algorithms rk2 / rk4 for a linear
-//     autonomous system and differs from them only by rounding;
+// A handle holds a batch of one or more problems of the same polynomial order
+// and precision (meshes, materials, frequencies and step counts may differ).
+// Problems are concatenated tile-wise in the device layout; every stage launch
+// covers all of them in lockstep, each problem reading its own coefficients
+// (step size, source phase, filter weights, whether it is still stepping) from
+// a per-launch table built once at creation.  Sweeps therefore never depend on
+// host data at run time.
+//
+// Sweeps (Section 4.1.2, Algorithms rk2 / rk4).  The state being propagated
+// lives in the work vector Uw.
+//   * source-free sweeps (P_w, P*_w) use the nested form of the RK polynomial,
+//     v <- U + (dt / k) B v for k = s, ..., 1, which is the same polynomial
+//     sum_k (dt B)^k / k! as Algorithms rk2 / rk4 for a linear autonomous system
+//     and differs from them only by rounding;
 //   * sweeps with the source (P_{psi,w}, F_{psi,w}) run Algorithms rk2 / rk4 as
 //     printed, with Phi(t, U) evaluated at the stage times; the filter is
 //     accumulated on the fly at the first stage of every step and once more at
 //     t_M (Eq. filtering_RK2 / filtering_RK4, each with the 2/T of Eq. filter).
 // CMCG (Section 2.2, Algorithms init / grad / cmcg) runs in residual form from
-// U0 = 0: G = P_psi 0, G* = G - P* G, R = D = G*, then per iteration
-// W_T = P D - D, A = P* W_T - W_T, alpha = |R|^2 / (D, A), U0 += alpha D,
-// R -= alpha A, beta = |R_new|^2 / |R|^2, D = R + beta D; the scalars are FP64
-// and stay on the device.
+// U0 = 0 for every problem: G = P_psi 0, G* = G - P* G, R = D = G*, then per
+// iteration W_T = P D - D, A = P* W_T - W_T, alpha = |R|^2 / (D, A),
+// U0 += alpha D, R -= alpha A, beta = |R_new|^2 / |R|^2, D = R + beta D.  The
+// scalars are FP64 and stay on the device, one set per problem; a problem
+// whose residual meets the tolerance stops sweeping and updating.
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <complex>
 #include <cstring>
@@ -28,35 +35,58 @@
 
 using namespace cmcg;
 
-struct cmcg_handle {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  HostLayout L;
-  int q = 1, np = 4, prec = CMCG_FP64, integrator = 2;
-  double omega = 0, T = 0, dt = 0;
+namespace {
+
+struct Prob {
+  int64_t nt = 0;                     // external tetrahedra
+  int64_t tet0 = 0, nti = 0;          // internal range
+  int64_t tile0 = 0, ntiles = 0;
+  int64_t ext0 = 0;                   // prefix of external tetrahedra
   int M = 0;
-  int64_t nt = 0, nti = 0, nvec = 0, njvec = 0;
+  double dt = 0, T = 0, omega = 0;
+  std::vector<std::complex<double>> fa, fb;  // filter weights per step 0..M (with 2/T)
+};
+
+}  // namespace
+
+struct cmcg_handle {
+  int device = 0, nsm = 0;
+  cudaStream_t stream = nullptr;
+  int q = 1, np = 4, prec = CMCG_FP64, s = 2, nprob = 1;
+  std::vector<Prob> P;
+  int64_t nti = 0, ntiles = 0, nvec = 0, njvec = 0, nt_total = 0;
   size_t rsize = 8;
-  // device memory
+  int maxM = 0;
+  // device geometry
   void *gvol = nullptr, *gface = nullptr;
   int32_t* nbr = nullptr;
   double* wdot = nullptr;
-  int32_t* e_of_i = nullptr;
-  double* inv_eps = nullptr;
+  int32_t* e_of_i = nullptr;  // internal tet -> external index within its problem (-1 = padding)
+  int32_t* tprob = nullptr;   // problem of each tile (nullptr when nprob == 1)
+  double* inv_eps = nullptr;  // external order, problems concatenated
+  // vectors
   void *Uw = nullptr, *vA = nullptr, *vB = nullptr, *ACC = nullptr, *Fre = nullptr, *Fim = nullptr;
   void *Jre = nullptr, *Jim = nullptr;
   void *U0 = nullptr, *Rv = nullptr, *D = nullptr, *A = nullptr, *WT = nullptr;
+  // CG
   double* partials = nullptr;
   Scalars* sc = nullptr;
   Scalars* sc_host = nullptr;  // pinned
+  int32_t* pactive = nullptr;
+  int32_t* pactive_host = nullptr;  // pinned
+  int64_t* bt_tet0 = nullptr;
+  int32_t *bt_ntet = nullptr, *bt_prob = nullptr, *bt_pb0 = nullptr;
+  BlockTable bt{};
+  // per-launch coefficient tables
+  void *tab_free = nullptr, *tab_src = nullptr, *tab_srcf = nullptr, *tab_one = nullptr;
+  int L_free = 0, L_src = 0, L_srcf = 0;
+  // staging for host I/O (nt_total * 6 * np doubles each)
   double *ext0 = nullptr, *ext1 = nullptr, *ext2 = nullptr, *ext3 = nullptr;
   int64_t launches = 0;
   size_t bytes = 0;
-  int variant = 0;     // occupancy variant of the per-stage kernel
-  int packed_minb = 0; // > 0 (FP32): every stage runs on the packed two-tetrahedra-per-lane kernel
-  int nsm = 0;
+  int variant = 0;      // occupancy variant of the scalar stage kernel
+  int packed_minb = 0;  // > 0 (FP32): stages run on the packed two-tetrahedra-per-lane kernel
   double tune_us[8];
-  std::vector<std::complex<double>> fa, fb;  // filter weights per step 0..M
   // sweep profiling
   bool prof = false;
   struct SweepEv {
@@ -82,9 +112,9 @@ int cuda_fail(cudaError_t e) {
   return CMCG_ERR_CUDA;
 }
 
-#define CK(expr)                               \
-  do {                                         \
-    cudaError_t e_ = (expr);                   \
+#define CK(expr)                                 \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
     if (e_ != cudaSuccess) return cuda_fail(e_); \
   } while (0)
 
@@ -106,16 +136,16 @@ int ensure_constants(int device, int q) {
 // The Hermite moments I_k(theta) = int_0^1 s^k e^{-i theta s} ds are computed
 // with a 24-point Gauss-Legendre rule (exact to rounding for the small theta
 // = w dt of a stable step).
-void filter_weights(cmcg_handle* h) {
-  const int M = h->M;
-  const double dt = h->dt, w = h->omega, c = 2.0 / h->T;
-  h->fa.assign(M + 1, 0.0);
-  h->fb.assign(M + 1, 0.0);
+void filter_weights(Prob& P, int integrator) {
+  const int M = P.M;
+  const double dt = P.dt, w = P.omega, c = 2.0 / P.T;
+  P.fa.assign(M + 1, 0.0);
+  P.fb.assign(M + 1, 0.0);
   using cd = std::complex<double>;
-  if (h->integrator == 2) {
+  if (integrator == 2) {
     for (int m = 0; m <= M; ++m) {
       const double wt = (m == 0 || m == M) ? 0.5 : 1.0;
-      h->fa[m] = c * dt * wt * std::exp(cd(0, -w * m * dt));
+      P.fa[m] = c * dt * wt * std::exp(cd(0, -w * m * dt));
     }
     return;
   }
@@ -138,11 +168,86 @@ void filter_weights(cmcg_handle* h) {
   const cd x10 = dt * (I[1] - 2.0 * I[2] + I[3]), x11 = dt * (I[3] - I[2]);
   for (int m = 1; m <= M; ++m) {
     const cd e = dt * std::exp(cd(0, -w * (m - 1) * dt));
-    h->fa[m - 1] += c * e * x00;
-    h->fa[m] += c * e * x01;
-    h->fb[m - 1] += c * e * x10;
-    h->fb[m] += c * e * x11;
+    P.fa[m - 1] += c * e * x00;
+    P.fa[m] += c * e * x01;
+    P.fb[m - 1] += c * e * x10;
+    P.fb[m] += c * e * x11;
   }
+}
+
+// Coefficient tables.  Launch l of a sweep is stage r = l % s of step m = l / s.
+// Classic stage r of RK4 (Algorithm rk4): out = U + c_out K_{r+1} (r < 3) or
+// ACC + dt/6 K4, acc = U + dt/6 K1 (r = 0), acc += dt/3 K_{r+1} (r = 1, 2); the
+// source is evaluated at t_m + {0, dt/2, dt/2, dt}.  RK2 (Algorithm rk2): out = U
+// + dt/2 K1 (r = 0), out = U + dt K2 at t_m + dt/2 (r = 1).
+template <typename R>
+void classic_coef(int s, int r, double dt, double t_m, double w, StageCoef<R>& c) {
+  static const double c4[4] = {0.5, 0.5, 1.0, 1.0 / 6.0}, a4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 0.0},
+                      o4[4] = {0.0, 0.5, 0.5, 1.0}, c2[2] = {0.5, 1.0}, o2[2] = {0.0, 0.5};
+  const double co = s == 4 ? c4[r] : c2[r], ca = s == 4 ? a4[r] : 0.0, off = s == 4 ? o4[r] : o2[r];
+  const double t = t_m + off * dt;
+  c.c_out = R(co * dt);
+  c.c_acc = R(ca * dt);
+  c.s_cos = R(std::cos(w * t));
+  c.s_sin = R(std::sin(w * t));
+}
+
+template <typename R>
+int build_tables(cmcg_handle* h) {
+  const int s = h->s, np_ = h->nprob;
+  h->L_free = h->maxM * s;
+  h->L_src = h->maxM * s;
+  h->L_srcf = h->maxM * s + 1;
+  std::vector<StageCoef<R>> tf(size_t(h->L_free) * np_), ts(size_t(h->L_src) * np_), tsf(size_t(h->L_srcf) * np_);
+  StageCoef<R> zero;
+  std::memset(&zero, 0, sizeof(zero));
+  for (int l = 0; l < h->L_srcf; ++l) {
+    const int m = l / s, r = l % s;
+    for (int p = 0; p < np_; ++p) {
+      const Prob& P = h->P[p];
+      if (l < h->L_free) {
+        StageCoef<R> c = zero;
+        if (m < P.M) {
+          c.active = 1;
+          c.c_out = R(P.dt / (s - r));
+        }
+        tf[size_t(l) * np_ + p] = c;
+        StageCoef<R> cs = zero;
+        if (m < P.M) {
+          cs.active = 1;
+          classic_coef<R>(s, r, P.dt, m * P.dt, P.omega, cs);
+        }
+        ts[size_t(l) * np_ + p] = cs;
+      }
+      StageCoef<R> cf = zero;
+      if (m < P.M || (m == P.M && r == 0)) {  // the extra launch at t_M evaluates Phi_M for the filter
+        cf.active = 1;
+        classic_coef<R>(s, r, P.dt, m * P.dt, P.omega, cf);
+        if (r == 0) {
+          cf.fa_re = R(P.fa[m].real());
+          cf.fa_im = R(P.fa[m].imag());
+          cf.fb_re = R(P.fb[m].real());
+          cf.fb_im = R(P.fb[m].imag());
+        }
+      }
+      tsf[size_t(l) * np_ + p] = cf;
+    }
+  }
+  const size_t sz = sizeof(StageCoef<R>);
+  CK(cudaMalloc(&h->tab_free, tf.size() * sz));
+  CK(cudaMalloc(&h->tab_src, ts.size() * sz));
+  CK(cudaMalloc(&h->tab_srcf, tsf.size() * sz));
+  CK(cudaMalloc(&h->tab_one, size_t(np_) * sz));
+  CK(cudaMemcpy(h->tab_free, tf.data(), tf.size() * sz, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->tab_src, ts.data(), ts.size() * sz, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->tab_srcf, tsf.data(), tsf.size() * sz, cudaMemcpyHostToDevice));
+  h->bytes += (tf.size() + ts.size() + tsf.size() + np_) * sz;
+  return CMCG_OK;
+}
+
+template <typename R>
+const StageCoef<R>* tab(void* t, int l, int nprob) {
+  return static_cast<const StageCoef<R>*>(t) + size_t(l) * nprob;
 }
 
 template <typename R>
@@ -151,6 +256,7 @@ void stage(cmcg_handle* h, StageArgs<R>& a) {
   a.gface = (const R*)h->gface;
   a.nbr = h->nbr;
   a.nti = h->nti;
+  a.tprob = h->tprob;
   if constexpr (sizeof(R) == 4) {
     if (h->packed_minb > 0) {
       if (h->q == 1) launch_stage_packed<1>(a, h->stream, h->packed_minb);
@@ -193,7 +299,6 @@ void prof_end(cmcg_handle* h, cmcg_handle::SweepEv* e) {
   cudaEventRecord(e->b, h->stream);
   e->stages = h->launches - e->stages;
 }
-// Folds recorded sweeps into the totals (waits for their events).
 void prof_collect(cmcg_handle* h) {
   for (size_t i = 0; i < h->prof_used; ++i) {
     cmcg_handle::SweepEv& e = h->prof_ev[i];
@@ -206,32 +311,31 @@ void prof_collect(cmcg_handle* h) {
   h->prof_used = 0;
 }
 
-// Source-free sweep of Uw in place (nested RK form); adjoint flips the magnetic sign.
+// Source-free sweep of Uw in place (nested RK form); adjoint flips the magnetic
+// sign.  pactive: skip problems whose CG has stopped (nullptr: sweep all).
 template <typename R>
-void sweep_free(cmcg_handle* h, bool adjoint) {
+void sweep_free(cmcg_handle* h, bool adjoint, const int32_t* pactive) {
   cmcg_handle::SweepEv* pe = prof_begin(h, false);
   R* Uw = (R*)h->Uw;
-  R* v[2] = {(R*)h->vA, (R*)h->vB};
-  const int s = h->integrator;
-  for (int m = 0; m < h->M; ++m) {
-    const R* vin = Uw;
-    int pp = 0;
-    for (int k = s; k >= 1; --k) {
-      StageArgs<R> a = blank<R>();
-      a.vin = vin;
-      a.base = Uw;
-      a.out = (k == 1) ? Uw : v[pp];
-      a.c_out = R(h->dt / k);
-      a.sH = adjoint ? R(-1) : R(1);
-      stage<R>(h, a);
-      vin = a.out;
-      pp ^= 1;
-    }
+  R* vA = (R*)h->vA;
+  R* vB = (R*)h->vB;
+  const int s = h->s;
+  for (int l = 0; l < h->L_free; ++l) {
+    const int r = l % s;
+    StageArgs<R> a = blank<R>();
+    a.vin = r == 0 ? Uw : (r % 2 == 1 ? vA : vB);
+    a.base = Uw;
+    a.out = r == s - 1 ? Uw : (r % 2 == 0 ? vA : vB);
+    a.sH = adjoint ? R(-1) : R(1);
+    a.coef = tab<R>(h->tab_free, l, h->nprob);
+    a.pactive = pactive;
+    stage<R>(h, a);
   }
   prof_end(h, pe);
 }
 
-// Sweep with source (Algorithms rk2 / rk4 as printed) of Uw in place; optional on-the-fly filter.
+// Sweep with source (Algorithms rk2 / rk4 as printed) of Uw in place; optional
+// on-the-fly filter (one extra launch evaluates Phi at t_M).
 template <typename R>
 void sweep_source(cmcg_handle* h, bool with_source, bool filter) {
   cmcg_handle::SweepEv* pe = prof_begin(h, true);
@@ -239,71 +343,43 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter) {
   R* vA = (R*)h->vA;
   R* vB = (R*)h->vB;
   R* ACC = (R*)h->ACC;
-  const double dt = h->dt, w = h->omega;
-  auto src = [&](StageArgs<R>& a, double t) {
-    if (!with_source) return;
-    a.jre = (const R*)h->Jre;
-    a.jim = (const R*)h->Jim;
-    a.s_cos = R(std::cos(w * t));
-    a.s_sin = R(std::sin(w * t));
-  };
-  auto filt = [&](StageArgs<R>& a, int m) {
-    if (!filter) return;
-    a.fre = (R*)h->Fre;
-    a.fim = (R*)h->Fim;
-    a.fa_re = R(h->fa[m].real());
-    a.fa_im = R(h->fa[m].imag());
-    a.fb_re = R(h->fb[m].real());
-    a.fb_im = R(h->fb[m].imag());
-  };
-  for (int m = 0; m < h->M; ++m) {
-    const double t = m * dt;
-    if (h->integrator == 2) {
-      StageArgs<R> a = blank<R>();
-      a.vin = Uw; a.base = Uw; a.out = vA; a.c_out = R(dt / 2);
-      src(a, t);
-      filt(a, m);
-      stage<R>(h, a);
-      StageArgs<R> b = blank<R>();
-      b.vin = vA; b.base = Uw; b.out = Uw; b.c_out = R(dt);
-      src(b, t + dt / 2);
-      stage<R>(h, b);
-    } else {
-      StageArgs<R> a = blank<R>();
-      a.vin = Uw; a.base = Uw; a.out = vA; a.c_out = R(dt / 2);
-      a.acc_in = Uw; a.acc_out = ACC; a.c_acc = R(dt / 6);
-      src(a, t);
-      filt(a, m);
-      stage<R>(h, a);
-      StageArgs<R> b = blank<R>();
-      b.vin = vA; b.base = Uw; b.out = vB; b.c_out = R(dt / 2);
-      b.acc_in = ACC; b.acc_out = ACC; b.c_acc = R(dt / 3);
-      src(b, t + dt / 2);
-      stage<R>(h, b);
-      StageArgs<R> c = blank<R>();
-      c.vin = vB; c.base = Uw; c.out = vA; c.c_out = R(dt);
-      c.acc_in = ACC; c.acc_out = ACC; c.c_acc = R(dt / 3);
-      src(c, t + dt / 2);
-      stage<R>(h, c);
-      StageArgs<R> d = blank<R>();
-      d.vin = vA; d.base = ACC; d.out = Uw; d.c_out = R(dt / 6);
-      src(d, t + dt);
-      stage<R>(h, d);
-    }
-  }
-  if (filter) {  // the t_M term: F += a_M U_M + b_M Phi(t_M, U_M)
+  const int s = h->s;
+  const int L = filter ? h->L_srcf : h->L_src;
+  void* table = filter ? h->tab_srcf : h->tab_src;
+  for (int l = 0; l < L; ++l) {
+    const int r = l % s;
     StageArgs<R> a = blank<R>();
-    a.vin = Uw;
-    src(a, h->M * dt);
-    filt(a, h->M);
+    if (s == 2) {
+      a.vin = r == 0 ? Uw : vA;
+      a.base = Uw;
+      a.out = r == 0 ? vA : Uw;
+    } else {
+      R* vin_of[4] = {Uw, vA, vB, vA};
+      a.vin = vin_of[r];
+      a.base = r == 3 ? ACC : Uw;
+      a.out = r == 0 ? vA : r == 1 ? vB : r == 2 ? vA : Uw;
+      if (r < 3) {
+        a.acc_in = r == 0 ? Uw : ACC;
+        a.acc_out = ACC;
+      }
+    }
+    if (with_source) {
+      a.jre = (const R*)h->Jre;
+      a.jim = (const R*)h->Jim;
+    }
+    if (filter && r == 0) {
+      a.fre = (R*)h->Fre;
+      a.fim = (R*)h->Fim;
+    }
+    a.coef = tab<R>(table, l, h->nprob);
     stage<R>(h, a);
   }
   prof_end(h, pe);
 }
 
-// Times the stage-kernel forms on this mesh with a nested source-free stage on
-// zero fields (3 warm-up + 12 timed launches each): the scalar kernel at each
-// occupancy variant and, in FP32, the packed kernel; keeps the fastest.
+// Times the stage-kernel forms on this batch with a nested source-free stage
+// on zero fields (3 warm-up + 12 timed launches each): the scalar kernel at
+// each occupancy variant and, in FP32, the packed kernel; keeps the fastest.
 // tune_us[0..2]: scalar variants, tune_us[3]: packed.
 template <typename R>
 int autotune(cmcg_handle* h, int nvariants) {
@@ -312,6 +388,7 @@ int autotune(cmcg_handle* h, int nvariants) {
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   CK(cudaMemsetAsync(h->Uw, 0, h->nvec * h->rsize, h->stream));
+  CK(cudaMemsetAsync(h->vB, 0, h->nvec * h->rsize, h->stream));
   const int64_t launches0 = h->launches;
   auto time_one = [&](double* us) -> int {
     auto run = [&](int n) {
@@ -320,7 +397,7 @@ int autotune(cmcg_handle* h, int nvariants) {
         a.vin = (const R*)h->Uw;
         a.base = (const R*)h->vB;
         a.out = (R*)h->vA;
-        a.c_out = R(h->dt);
+        a.coef = tab<R>(h->tab_free, 0, h->nprob);
         stage<R>(h, a);
       }
     };
@@ -340,7 +417,6 @@ int autotune(cmcg_handle* h, int nvariants) {
     *us = 1e3 * ms / 12;
     return CMCG_OK;
   };
-  CK(cudaMemsetAsync(h->vB, 0, h->nvec * h->rsize, h->stream));
   double best = 1e300;
   int bestv = 0;
   h->packed_minb = 0;
@@ -371,15 +447,21 @@ int autotune(cmcg_handle* h, int nvariants) {
   return CMCG_OK;
 }
 
+// Per-problem layout conversion.
 template <typename R>
-void to_int(cmcg_handle* h, const double* ext, int ncomp_ext, R* in, int ncomp_in, int c_in0, int cnt,
+void to_int(cmcg_handle* h, int p, const double* ext, int ncomp_ext, void* in, int ncomp_in, int cnt,
             const double* per_tet) {
-  launch_to_internal<R>(ext, ncomp_ext, 0, in, ncomp_in, c_in0, cnt, h->e_of_i, h->nti, h->np, 1.0, per_tet, h->stream);
+  const Prob& P = h->P[p];
+  R* base = (R*)in + P.tile0 * int64_t(ncomp_in) * h->np * TILE;
+  launch_to_internal<R>(ext, ncomp_ext, 0, base, ncomp_in, 0, cnt, h->e_of_i + P.tet0, P.nti, h->np, 1.0,
+                        per_tet ? per_tet + P.ext0 : nullptr, h->stream);
   h->launches++;
 }
 template <typename R>
-void to_ext(cmcg_handle* h, const R* in, int ncomp_in, int c_in0, double* ext, int ncomp_ext, int cnt) {
-  launch_to_external<R>(in, ncomp_in, c_in0, ext, ncomp_ext, 0, cnt, h->e_of_i, h->nti, h->np, h->stream);
+void to_ext(cmcg_handle* h, int p, const void* in, int ncomp_in, int c_in0, double* ext, int ncomp_ext, int cnt) {
+  const Prob& P = h->P[p];
+  const R* base = (const R*)in + P.tile0 * int64_t(ncomp_in) * h->np * TILE;
+  launch_to_external<R>(base, ncomp_in, c_in0, ext, ncomp_ext, 0, cnt, h->e_of_i + P.tet0, P.nti, h->np, h->stream);
   h->launches++;
 }
 template <typename R>
@@ -389,21 +471,29 @@ void lincomb(cmcg_handle* h, void* o1, void* o2, void* o3, double a, const void*
 }
 
 template <typename R>
-int set_source(cmcg_handle* h, const double* j_re, const double* j_im) {
-  to_int<R>(h, j_re, 3, (R*)h->Jre, 3, 0, 3, h->inv_eps);
-  if (j_im) to_int<R>(h, j_im, 3, (R*)h->Jim, 3, 0, 3, h->inv_eps);
-  else CK(cudaMemsetAsync(h->Jim, 0, h->njvec * h->rsize, h->stream));
+int set_source(cmcg_handle* h, const double* const* j_re, const double* const* j_im) {
+  for (int p = 0; p < h->nprob; ++p) {
+    to_int<R>(h, p, j_re[p], 3, h->Jre, 3, 3, h->inv_eps);
+    const double* ji = j_im ? j_im[p] : nullptr;
+    if (ji) {
+      to_int<R>(h, p, ji, 3, h->Jim, 3, 3, h->inv_eps);
+    } else {
+      const Prob& P = h->P[p];
+      CK(cudaMemsetAsync((char*)h->Jim + P.tile0 * 3 * h->np * TILE * h->rsize, 0,
+                         size_t(P.ntiles) * 3 * h->np * TILE * h->rsize, h->stream));
+    }
+  }
   return CMCG_OK;
 }
 
-// Device-pointer period sweeps.
+// Device-pointer period sweeps of a one-problem handle.
 template <typename R>
 int forward_dev(cmcg_handle* h, const double* u0, const double* j_re, const double* j_im, double* uT, double* fre,
                 double* fim) {
-  to_int<R>(h, u0, 6, (R*)h->Uw, 6, 0, 6, nullptr);
+  to_int<R>(h, 0, u0, 6, h->Uw, 6, 6, nullptr);
   const bool filter = fre && fim;
   if (j_re) {
-    int rc = set_source<R>(h, j_re, j_im);
+    int rc = set_source<R>(h, &j_re, &j_im);
     if (rc) return rc;
   }
   if (filter) {
@@ -411,11 +501,11 @@ int forward_dev(cmcg_handle* h, const double* u0, const double* j_re, const doub
     CK(cudaMemsetAsync(h->Fim, 0, h->nvec * h->rsize, h->stream));
   }
   if (j_re || filter) sweep_source<R>(h, j_re != nullptr, filter);
-  else sweep_free<R>(h, false);
-  if (uT) to_ext<R>(h, (const R*)h->Uw, 6, 0, uT, 6, 6);
+  else sweep_free<R>(h, false, nullptr);
+  if (uT) to_ext<R>(h, 0, h->Uw, 6, 0, uT, 6, 6);
   if (filter) {
-    to_ext<R>(h, (const R*)h->Fre, 6, 0, fre, 6, 6);
-    to_ext<R>(h, (const R*)h->Fim, 6, 0, fim, 6, 6);
+    to_ext<R>(h, 0, h->Fre, 6, 0, fre, 6, 6);
+    to_ext<R>(h, 0, h->Fim, 6, 0, fim, 6, 6);
   }
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
@@ -424,9 +514,9 @@ int forward_dev(cmcg_handle* h, const double* u0, const double* j_re, const doub
 
 template <typename R>
 int adjoint_dev(cmcg_handle* h, const double* wT, double* w0) {
-  to_int<R>(h, wT, 6, (R*)h->Uw, 6, 0, 6, nullptr);
-  sweep_free<R>(h, true);
-  to_ext<R>(h, (const R*)h->Uw, 6, 0, w0, 6, 6);
+  to_int<R>(h, 0, wT, 6, h->Uw, 6, 6, nullptr);
+  sweep_free<R>(h, true, nullptr);
+  to_ext<R>(h, 0, h->Uw, 6, 0, w0, 6, 6);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return CMCG_OK;
@@ -435,24 +525,29 @@ int adjoint_dev(cmcg_handle* h, const double* wT, double* w0) {
 template <typename R>
 int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, const double* j_im, int adjoint,
               double* out) {
-  to_int<R>(h, u, 6, (R*)h->Uw, 6, 0, 6, nullptr);
+  to_int<R>(h, 0, u, 6, h->Uw, 6, 6, nullptr);
   CK(cudaMemsetAsync(h->vB, 0, h->nvec * h->rsize, h->stream));
+  StageCoef<R> c;
+  std::memset(&c, 0, sizeof(c));
+  c.active = 1;
+  c.c_out = R(1);
+  c.s_cos = R(std::cos(h->P[0].omega * t));
+  c.s_sin = R(std::sin(h->P[0].omega * t));
+  CK(cudaMemcpy(h->tab_one, &c, sizeof(c), cudaMemcpyHostToDevice));
   StageArgs<R> a = blank<R>();
   a.vin = (const R*)h->Uw;
   a.base = (const R*)h->vB;
   a.out = (R*)h->vA;
-  a.c_out = R(1);
   a.sH = adjoint ? R(-1) : R(1);
+  a.coef = (const StageCoef<R>*)h->tab_one;
   if (j_re && !adjoint) {
-    int rc = set_source<R>(h, j_re, j_im);
+    int rc = set_source<R>(h, &j_re, &j_im);
     if (rc) return rc;
     a.jre = (const R*)h->Jre;
     a.jim = (const R*)h->Jim;
-    a.s_cos = R(std::cos(h->omega * t));
-    a.s_sin = R(std::sin(h->omega * t));
   }
   stage<R>(h, a);
-  to_ext<R>(h, (const R*)h->vA, 6, 0, out, 6, 6);
+  to_ext<R>(h, 0, h->vA, 6, 0, out, 6, 6);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
   return CMCG_OK;
@@ -460,86 +555,83 @@ int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, con
 
 template <typename R>
 int inner_dev(cmcg_handle* h, const double* u, const double* v, double* out) {
-  to_int<R>(h, u, 6, (R*)h->Uw, 6, 0, 6, nullptr);
-  to_int<R>(h, v, 6, (R*)h->vA, 6, 0, 6, nullptr);
-  launch_dot<R>(h->q, (const R*)h->Uw, (const R*)h->vA, h->wdot, h->partials, h->nti, h->stream);
-  launch_finalize(h->partials, dot_blocks(h->nti), h->sc, 3, h->stream);
+  to_int<R>(h, 0, u, 6, h->Uw, 6, 6, nullptr);
+  to_int<R>(h, 0, v, 6, h->vA, 6, 6, nullptr);
+  launch_dot<R>(h->q, (const R*)h->Uw, (const R*)h->vA, h->wdot, h->partials, h->bt, h->stream);
+  launch_finalize(h->partials, h->bt, h->sc, nullptr, 3, 0.0, h->stream);
   h->launches += 2;
   CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  *out = h->sc_host->rr_new;
+  *out = h->sc_host[0].rr_new;
   return CMCG_OK;
 }
 
-template <typename R>
-int read_scalars(cmcg_handle* h) {
-  CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+int read_state(cmcg_handle* h) {
+  CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars) * h->nprob, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->pactive_host, h->pactive, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return CMCG_OK;
 }
 
+// CMCG for every problem of the handle; j, e, h: one device pointer per problem.
 template <typename R>
-int solve_dev(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
-              double* e_im, double* h_re, double* h_im, cmcg_info* info) {
+int solve_dev(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol, int max_iter,
+              double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im, cmcg_info* info) {
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   CK(cudaEventRecord(ev0, h->stream));
-  const int nb = dot_blocks(h->nti);
   int rc = set_source<R>(h, j_re, j_im);
   if (rc) return rc;
-  CK(cudaMemsetAsync(h->sc, 0, sizeof(Scalars), h->stream));
+  CK(cudaMemsetAsync(h->sc, 0, sizeof(Scalars) * h->nprob, h->stream));
   // Algorithm init: G = P_psi 0, G_T = P* G, G* = G - G_T.
   CK(cudaMemsetAsync(h->Uw, 0, h->nvec * h->rsize, h->stream));
   sweep_source<R>(h, true, false);
   lincomb<R>(h, h->A, nullptr, nullptr, 1.0, h->Uw, 0.0, nullptr);
-  sweep_free<R>(h, true);
+  sweep_free<R>(h, true, nullptr);
   lincomb<R>(h, h->Rv, h->D, h->Uw, 1.0, h->A, -1.0, h->Uw);  // R = D = G*, Uw = D
   CK(cudaMemsetAsync(h->U0, 0, h->nvec * h->rsize, h->stream));
-  launch_dot<R>(h->q, (const R*)h->Rv, (const R*)h->Rv, h->wdot, h->partials, h->nti, h->stream);
-  launch_finalize(h->partials, nb, h->sc, 0, h->stream);
+  launch_dot<R>(h->q, (const R*)h->Rv, (const R*)h->Rv, h->wdot, h->partials, h->bt, h->stream);
+  launch_finalize(h->partials, h->bt, h->sc, h->pactive, 0, tol, h->stream);
   h->launches += 2;
-  rc = read_scalars<R>(h);
+  rc = read_state(h);
   if (rc) return rc;
-  const double rr0 = h->sc_host->rr0;
-  double rr = h->sc_host->rr;
+  auto any_active = [&]() {
+    for (int p = 0; p < h->nprob; ++p)
+      if (h->pactive_host[p]) return true;
+    return false;
+  };
   int it = 0;
-  int status = CMCG_OK;
-  bool converged = !(rr0 > 0);
-  if (!std::isfinite(rr0)) status = CMCG_ERR_NONFINITE;
-  while (status == CMCG_OK && !converged && it < max_iter) {
-    if (std::sqrt(rr) <= tol * std::sqrt(rr0)) {
-      converged = true;
-      break;
-    }
+  while (any_active() && it < max_iter) {
     // Algorithm grad on D: W_T = P D - D; A = P* W_T - W_T.
-    sweep_free<R>(h, false);
+    sweep_free<R>(h, false, h->pactive);
     lincomb<R>(h, h->WT, h->Uw, nullptr, 1.0, h->Uw, -1.0, h->D);
-    sweep_free<R>(h, true);
+    sweep_free<R>(h, true, h->pactive);
     launch_cg_after_adjoint<R>(h->q, (const R*)h->Uw, (const R*)h->WT, (R*)h->A, (const R*)h->D, h->wdot, h->partials,
-                               h->nti, h->stream);
-    launch_finalize(h->partials, nb, h->sc, 1, h->stream);
-    launch_cg_update<R>(h->q, (R*)h->U0, (R*)h->Rv, (const R*)h->D, (const R*)h->A, h->wdot, h->sc, h->partials, h->nti,
-                        h->stream);
-    launch_finalize(h->partials, nb, h->sc, 2, h->stream);
-    launch_cg_direction<R>((R*)h->D, (R*)h->Uw, (const R*)h->Rv, h->sc, h->nvec, h->stream);
+                               h->bt, h->pactive, h->stream);
+    launch_finalize(h->partials, h->bt, h->sc, h->pactive, 1, tol, h->stream);
+    launch_cg_update<R>(h->q, (R*)h->U0, (R*)h->Rv, (const R*)h->D, (const R*)h->A, h->wdot, h->sc, h->partials, h->bt,
+                        h->pactive, h->stream);
+    launch_finalize(h->partials, h->bt, h->sc, h->pactive, 2, tol, h->stream);
+    // problems that just converged keep D; the others get D = R + beta D, Uw = D
+    launch_cg_direction<R>((R*)h->D, (R*)h->Uw, (const R*)h->Rv, h->sc, h->tprob, h->pactive, h->nvec, h->np,
+                           h->stream);
     h->launches += 5;
     ++it;
-    rc = read_scalars<R>(h);
+    rc = read_state(h);
     if (rc) return rc;
-    if (h->sc_host->status != 0) status = h->sc_host->status;
-    rr = h->sc_host->rr;
   }
-  if (!converged && status == CMCG_OK && std::sqrt(rr) <= tol * std::sqrt(rr0)) converged = true;
-  // Final filter F_{psi,w} U0.
+  // Final filter F_{psi,w} U0 for every problem.
   lincomb<R>(h, h->Uw, nullptr, nullptr, 1.0, h->U0, 0.0, nullptr);
   CK(cudaMemsetAsync(h->Fre, 0, h->nvec * h->rsize, h->stream));
   CK(cudaMemsetAsync(h->Fim, 0, h->nvec * h->rsize, h->stream));
   sweep_source<R>(h, true, true);
-  to_ext<R>(h, (const R*)h->Fre, 6, 0, e_re, 3, 3);
-  to_ext<R>(h, (const R*)h->Fim, 6, 0, e_im, 3, 3);
-  to_ext<R>(h, (const R*)h->Fre, 6, 3, h_re, 3, 3);
-  to_ext<R>(h, (const R*)h->Fim, 6, 3, h_im, 3, 3);
+  for (int p = 0; p < h->nprob; ++p) {
+    to_ext<R>(h, p, h->Fre, 6, 0, e_re[p], 3, 3);
+    to_ext<R>(h, p, h->Fim, 6, 0, e_im[p], 3, 3);
+    to_ext<R>(h, p, h->Fre, 6, 3, h_re[p], 3, 3);
+    to_ext<R>(h, p, h->Fim, 6, 3, h_im[p], 3, 3);
+  }
   CK(cudaEventRecord(ev1, h->stream));
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
@@ -547,26 +639,39 @@ int solve_dev(cmcg_handle* h, const double* j_re, const double* j_im, double tol
   cudaEventElapsedTime(&ms, ev0, ev1);
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
-  if (status == CMCG_OK && !converged) status = CMCG_NOT_CONVERGED;
-  if (info) {
-    info->iters = it;
-    info->periods = 3 + 2 * it;
-    info->steps_per_period = h->M;
-    info->status = status;
-    info->rel_residual = rr0 > 0 ? std::sqrt(std::max(rr, 0.0) / rr0) : 0.0;
-    info->dt = h->dt;
-    info->solve_ms = ms;
+  int worst = CMCG_OK;
+  for (int p = 0; p < h->nprob; ++p) {
+    const Scalars& S = h->sc_host[p];
+    int st = S.status;
+    const bool conv = S.rr0 > 0 ? std::sqrt(std::max(S.rr, 0.0)) <= tol * std::sqrt(S.rr0) : true;
+    if (st == CMCG_OK && !conv) st = CMCG_NOT_CONVERGED;
+    if (st < 0) {
+      if (worst >= 0 || st < worst) worst = st;
+    } else if (worst >= 0 && st > worst) {
+      worst = st;
+    }
+    if (info) {
+      info[p].iters = S.iters;
+      info[p].periods = 3 + 2 * S.iters;
+      info[p].steps_per_period = h->P[p].M;
+      info[p].status = st;
+      info[p].rel_residual = S.rr0 > 0 ? std::sqrt(std::max(S.rr, 0.0) / S.rr0) : 0.0;
+      info[p].dt = h->P[p].dt;
+      info[p].solve_ms = ms;
+    }
   }
-  return status;
+  return worst;
 }
 
 void free_all(cmcg_handle* h) {
-  void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
-                  h->Fre, h->Fim, h->Jre, h->Jim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials,
-                  h->sc, h->ext0, h->ext1, h->ext2, h->ext3};
+  void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
+                  h->Fre, h->Fim, h->Jre, h->Jim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
+                  h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
+                  h->ext0, h->ext1, h->ext2, h->ext3};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->sc_host) cudaFreeHost(h->sc_host);
+  if (h->pactive_host) cudaFreeHost(h->pactive_host);
   for (auto& e : h->prof_ev) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -578,6 +683,174 @@ std::vector<R> cast(const std::vector<double>& v) {
   return std::vector<R>(v.begin(), v.end());
 }
 
+template <typename T>
+int upload(void** dst, const std::vector<T>& v, size_t* bytes) {
+  const size_t n = std::max<size_t>(1, v.size()) * sizeof(T);
+  CK(cudaMalloc(dst, n));
+  if (!v.empty()) CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *bytes += n;
+  return CMCG_OK;
+}
+
+int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in, cmcg_handle** out) {
+  if (!out) return CMCG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (nprob < 1 || !probs) return CMCG_ERR_INVALID_ARG;
+  cmcg_options opt;
+  if (opt_in) opt = *opt_in;
+  else cmcg_default_options(&opt);
+  cmcg_handle* h = new (std::nothrow) cmcg_handle();
+  if (!h) return CMCG_ERR_OUT_OF_MEMORY;
+  for (double& x : h->tune_us) x = -1;
+  h->device = opt.device;
+  h->q = opt.order;
+  h->prec = opt.precision;
+  h->s = opt.order == 1 ? 2 : 4;
+  h->nprob = nprob;
+  h->rsize = opt.precision == CMCG_FP32 ? 4 : 8;
+  h->P.resize(nprob);
+  // Host layouts, concatenated.
+  std::vector<double> gvol, gface, wdot, inv_eps;
+  std::vector<int32_t> nbr, e_of_i, tprob;
+  int rc = CMCG_OK;
+  try {
+    for (int p = 0; p < nprob && rc == CMCG_OK; ++p) {
+      HostLayout L;
+      std::string why;
+      rc = validate_and_layout(probs[p].mesh, probs[p].eps, probs[p].mu, probs[p].omega, &opt, &L, true, &why);
+      if (rc) break;
+      Prob& P = h->P[p];
+      P.nt = L.nt;
+      P.tet0 = h->nti;
+      P.nti = L.nti;
+      P.tile0 = h->ntiles;
+      P.ntiles = L.ntiles;
+      P.ext0 = h->nt_total;
+      P.M = L.steps;
+      P.dt = L.dt;
+      P.T = L.T;
+      P.omega = probs[p].omega;
+      filter_weights(P, h->s);
+      h->maxM = std::max(h->maxM, P.M);
+      if (h->nti + L.nti > (int64_t(1) << 26)) {  // neighbour codes hold 26-bit internal indices
+        rc = CMCG_ERR_INVALID_ARG;
+        break;
+      }
+      gvol.insert(gvol.end(), L.gvol.begin(), L.gvol.end());
+      gface.insert(gface.end(), L.gface.begin(), L.gface.end());
+      wdot.insert(wdot.end(), L.wdot.begin(), L.wdot.end());
+      const int32_t shift = int32_t(P.tet0) << 5;
+      for (int32_t c : L.nbr) nbr.push_back(c >= 0 ? c + shift : c);
+      e_of_i.insert(e_of_i.end(), L.ext_of_int.begin(), L.ext_of_int.end());
+      for (int64_t t = 0; t < L.ntiles; ++t) tprob.push_back(p);
+      for (int64_t k = 0; k < L.nt; ++k) inv_eps.push_back(1.0 / probs[p].eps[k]);
+      h->nti += L.nti;
+      h->ntiles += L.ntiles;
+      h->nt_total += L.nt;
+    }
+  } catch (const std::bad_alloc&) {
+    rc = CMCG_ERR_OUT_OF_MEMORY;
+  } catch (...) {
+    rc = CMCG_ERR_INVALID_ARG;
+  }
+  if (rc) {
+    delete h;
+    return rc;
+  }
+  h->np = np_of(h->q);
+  h->nvec = h->nti * 6 * h->np;
+  h->njvec = h->nti * 3 * h->np;
+  // Problem-aligned reduction blocks.
+  std::vector<int64_t> bt_tet0;
+  std::vector<int32_t> bt_ntet, bt_prob, bt_pb0;
+  for (int p = 0; p < nprob; ++p) {
+    bt_pb0.push_back(int32_t(bt_tet0.size()));
+    for (int64_t t = 0; t < h->P[p].nti; t += DOT_THREADS) {
+      bt_tet0.push_back(h->P[p].tet0 + t);
+      bt_ntet.push_back(int32_t(std::min<int64_t>(DOT_THREADS, h->P[p].nti - t)));
+      bt_prob.push_back(p);
+    }
+  }
+  bt_pb0.push_back(int32_t(bt_tet0.size()));
+
+  const size_t extlen = size_t(h->nt_total) * 6 * h->np * sizeof(double);
+  const size_t need = 11 * h->nvec * h->rsize + 2 * h->njvec * h->rsize + gvol.size() * h->rsize +
+                      gface.size() * h->rsize + nbr.size() * 4 + wdot.size() * 8 + e_of_i.size() * 4 +
+                      inv_eps.size() * 8 + 4 * extlen + bt_tet0.size() * 24 + size_t(nprob) * 128 +
+                      size_t(3 * h->maxM * h->s + 2) * nprob * sizeof(StageCoef<double>);
+  h->bytes = need;
+  if (opt.hbm_budget_bytes > 0 && (int64_t)need > opt.hbm_budget_bytes) {
+    delete h;
+    return CMCG_ERR_OUT_OF_MEMORY;
+  }
+  int ndev = 0;
+  cudaError_t ce = cudaGetDeviceCount(&ndev);
+  if (ce != cudaSuccess || ndev == 0) {
+    delete h;
+    return CMCG_ERR_NO_DEVICE;
+  }
+  if (opt.device < 0 || opt.device >= ndev) {
+    delete h;
+    return CMCG_ERR_INVALID_ARG;
+  }
+  auto fail = [&](int code) {
+    free_all(h);
+    delete h;
+    return code;
+  };
+  if (cudaSetDevice(opt.device) != cudaSuccess) return fail(CMCG_ERR_CUDA);
+  if ((rc = ensure_constants(opt.device, opt.order))) return fail(rc);
+  if (cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, opt.device) != cudaSuccess)
+    return fail(CMCG_ERR_CUDA);
+
+  size_t bytes = 0;
+  if (h->prec == CMCG_FP32) {
+    if ((rc = upload(&h->gvol, cast<float>(gvol), &bytes)) || (rc = upload(&h->gface, cast<float>(gface), &bytes)))
+      return fail(rc);
+  } else {
+    if ((rc = upload(&h->gvol, gvol, &bytes)) || (rc = upload(&h->gface, gface, &bytes))) return fail(rc);
+  }
+  if ((rc = upload((void**)&h->nbr, nbr, &bytes)) || (rc = upload((void**)&h->wdot, wdot, &bytes)) ||
+      (rc = upload((void**)&h->e_of_i, e_of_i, &bytes)) || (rc = upload((void**)&h->inv_eps, inv_eps, &bytes)) ||
+      (rc = upload((void**)&h->bt_tet0, bt_tet0, &bytes)) || (rc = upload((void**)&h->bt_ntet, bt_ntet, &bytes)) ||
+      (rc = upload((void**)&h->bt_prob, bt_prob, &bytes)) || (rc = upload((void**)&h->bt_pb0, bt_pb0, &bytes)))
+    return fail(rc);
+  if (nprob > 1 && (rc = upload((void**)&h->tprob, tprob, &bytes))) return fail(rc);
+  h->bt = BlockTable{h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, int(bt_tet0.size()), nprob};
+
+  auto alloc = [&](void** p, size_t n) -> bool { return cudaMalloc(p, n) == cudaSuccess; };
+  const size_t vb = h->nvec * h->rsize, jb = h->njvec * h->rsize;
+  bool ok = alloc(&h->Uw, vb) && alloc(&h->vA, vb) && alloc(&h->vB, vb) && alloc(&h->ACC, vb) && alloc(&h->Fre, vb) &&
+            alloc(&h->Fim, vb) && alloc(&h->Jre, jb) && alloc(&h->Jim, jb) && alloc(&h->U0, vb) &&
+            alloc(&h->Rv, vb) && alloc(&h->D, vb) && alloc(&h->A, vb) && alloc(&h->WT, vb) &&
+            alloc((void**)&h->partials, sizeof(double) * std::max<size_t>(1, bt_tet0.size())) &&
+            alloc((void**)&h->sc, sizeof(Scalars) * nprob) && alloc((void**)&h->pactive, sizeof(int32_t) * nprob) &&
+            alloc((void**)&h->ext0, extlen) && alloc((void**)&h->ext1, extlen) && alloc((void**)&h->ext2, extlen) &&
+            alloc((void**)&h->ext3, extlen);
+  if (!ok) return fail(CMCG_ERR_OUT_OF_MEMORY);
+  if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars) * nprob) != cudaSuccess ||
+      cudaMallocHost((void**)&h->pactive_host, sizeof(int32_t) * nprob) != cudaSuccess)
+    return fail(CMCG_ERR_OUT_OF_MEMORY);
+  if (cudaMemset(h->ACC, 0, vb) != cudaSuccess) return fail(CMCG_ERR_CUDA);
+  rc = h->prec == CMCG_FP32 ? build_tables<float>(h) : build_tables<double>(h);
+  if (rc) return fail(rc);
+  if (opt.stage_variant > 0) {
+    const int nv = h->prec == CMCG_FP32 ? STAGE_VARIANTS_F32 : 1;
+    const int k = opt.stage_variant - 1;
+    if (k < nv) h->variant = k;
+    else if (k == 3 && h->prec == CMCG_FP32) h->packed_minb = 2;
+    else return fail(CMCG_ERR_INVALID_ARG);
+  } else {
+    rc = h->prec == CMCG_FP32 ? autotune<float>(h, STAGE_VARIANTS_F32) : autotune<double>(h, 1);
+    if (rc) return fail(rc);
+  }
+  h->launches = 0;
+  *out = h;
+  return CMCG_OK;
+}
+
+bool single(const cmcg_handle* h) { return h && h->nprob == 1; }
+
 }  // namespace
 
 extern "C" {
@@ -588,10 +861,6 @@ void cmcg_default_options(cmcg_options* opt) {
   opt->order = 1;
   opt->precision = CMCG_FP64;
   opt->flux = CMCG_FLUX_UPWIND;
-  opt->steps_per_period = 0;
-  opt->c_q = 0.0;
-  opt->hbm_budget_bytes = 0;
-  opt->device = 0;
 }
 
 const char* cmcg_status_string(int s) {
@@ -648,125 +917,14 @@ int cmcg_reference_matrices(int order, double* mass, double* dr, double* ds, dou
   return CMCG_OK;
 }
 
-int cmcg_create(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega, const cmcg_options* opt_in,
+int cmcg_create(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega, const cmcg_options* opt,
                 cmcg_handle** out) {
-  if (!out) return CMCG_ERR_INVALID_ARG;
-  *out = nullptr;
-  cmcg_options opt;
-  if (opt_in) opt = *opt_in;
-  else cmcg_default_options(&opt);
-  cmcg_handle* h = new (std::nothrow) cmcg_handle();
-  if (!h) return CMCG_ERR_OUT_OF_MEMORY;
-  std::string why;
-  int rc;
-  try {
-    rc = validate_and_layout(mesh, eps, mu, omega, &opt, &h->L, true, &why);
-  } catch (const std::bad_alloc&) {
-    rc = CMCG_ERR_OUT_OF_MEMORY;
-  } catch (...) {
-    rc = CMCG_ERR_INVALID_ARG;
-  }
-  if (rc) {
-    delete h;
-    return rc;
-  }
-  const HostLayout& L = h->L;
-  h->device = opt.device;
-  h->q = opt.order;
-  h->np = np_of(opt.order);
-  h->prec = opt.precision;
-  h->integrator = opt.order == 1 ? 2 : 4;
-  h->omega = omega;
-  h->T = L.T;
-  h->dt = L.dt;
-  h->M = L.steps;
-  h->nt = L.nt;
-  h->nti = L.nti;
-  h->nvec = L.nti * 6 * h->np;
-  h->njvec = L.nti * 3 * h->np;
-  h->rsize = opt.precision == CMCG_FP32 ? 4 : 8;
-  filter_weights(h);
+  const cmcg_problem p{mesh, eps, mu, omega};
+  return create_impl(1, &p, opt, out);
+}
 
-  const size_t extlen = size_t(L.nt) * 6 * h->np * sizeof(double);
-  const size_t need = 11 * h->nvec * h->rsize + 2 * h->njvec * h->rsize + L.gvol.size() * h->rsize +
-                      L.gface.size() * h->rsize + L.nbr.size() * 4 + L.wdot.size() * 8 + L.ext_of_int.size() * 4 +
-                      L.nt * 8 + 4 * extlen + 4096 * 8 + sizeof(Scalars);
-  h->bytes = need;
-  if (opt.hbm_budget_bytes > 0 && (int64_t)need > opt.hbm_budget_bytes) {
-    delete h;
-    return CMCG_ERR_OUT_OF_MEMORY;
-  }
-  int ndev = 0;
-  cudaError_t ce = cudaGetDeviceCount(&ndev);
-  if (ce != cudaSuccess || ndev == 0) {
-    delete h;
-    return CMCG_ERR_NO_DEVICE;
-  }
-  if (opt.device < 0 || opt.device >= ndev) {
-    delete h;
-    return CMCG_ERR_INVALID_ARG;
-  }
-  auto fail = [&](int code) {
-    free_all(h);
-    delete h;
-    return code;
-  };
-  if (cudaSetDevice(opt.device) != cudaSuccess) return fail(CMCG_ERR_CUDA);
-  if ((rc = ensure_constants(opt.device, opt.order))) return fail(rc);
-
-  auto alloc = [&](void** p, size_t bytes) -> bool { return cudaMalloc(p, bytes) == cudaSuccess; };
-  const size_t vb = h->nvec * h->rsize, jb = h->njvec * h->rsize;
-  bool ok = alloc(&h->gvol, L.gvol.size() * h->rsize) && alloc(&h->gface, L.gface.size() * h->rsize) &&
-            alloc((void**)&h->nbr, L.nbr.size() * 4) && alloc((void**)&h->wdot, L.wdot.size() * 8) &&
-            alloc((void**)&h->e_of_i, L.ext_of_int.size() * 4) && alloc((void**)&h->inv_eps, L.nt * 8) &&
-            alloc(&h->Uw, vb) && alloc(&h->vA, vb) && alloc(&h->vB, vb) && alloc(&h->ACC, vb) && alloc(&h->Fre, vb) &&
-            alloc(&h->Fim, vb) && alloc(&h->Jre, jb) && alloc(&h->Jim, jb) && alloc(&h->U0, vb) && alloc(&h->Rv, vb) &&
-            alloc(&h->D, vb) && alloc(&h->A, vb) && alloc(&h->WT, vb) &&
-            alloc((void**)&h->partials, sizeof(double) * 4096) && alloc((void**)&h->sc, sizeof(Scalars)) &&
-            alloc((void**)&h->ext0, extlen) && alloc((void**)&h->ext1, extlen) && alloc((void**)&h->ext2, extlen) &&
-            alloc((void**)&h->ext3, extlen);
-  if (!ok) return fail(CMCG_ERR_OUT_OF_MEMORY);
-  if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars)) != cudaSuccess) return fail(CMCG_ERR_OUT_OF_MEMORY);
-  std::vector<double> inv_eps(L.nt);
-  for (int64_t k = 0; k < L.nt; ++k) inv_eps[k] = 1.0 / eps[k];
-  cudaError_t e = cudaSuccess;
-  if (h->prec == CMCG_FP32) {
-    auto gv = cast<float>(L.gvol), gf = cast<float>(L.gface);
-    e = cudaMemcpy(h->gvol, gv.data(), gv.size() * 4, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(h->gface, gf.data(), gf.size() * 4, cudaMemcpyHostToDevice);
-  } else {
-    e = cudaMemcpy(h->gvol, L.gvol.data(), L.gvol.size() * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(h->gface, L.gface.data(), L.gface.size() * 8, cudaMemcpyHostToDevice);
-  }
-  if (e == cudaSuccess) e = cudaMemcpy(h->nbr, L.nbr.data(), L.nbr.size() * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->wdot, L.wdot.data(), L.wdot.size() * 8, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->e_of_i, L.ext_of_int.data(), L.ext_of_int.size() * 4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->inv_eps, inv_eps.data(), L.nt * 8, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(h->ACC, 0, vb);
-  if (e != cudaSuccess) return fail(cuda_fail(e));
-  {
-    int nsm = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, opt.device) != cudaSuccess) return fail(CMCG_ERR_CUDA);
-    h->nsm = nsm;
-  }
-  for (double& x : h->tune_us) x = -1;
-  if (opt.stage_variant > 0) {
-    const int nv = h->prec == CMCG_FP32 ? STAGE_VARIANTS_F32 : 1;
-    const int k = opt.stage_variant - 1;
-    if (k < nv) {
-      h->variant = k;
-    } else if (k == 3 && h->prec == CMCG_FP32) {
-      h->packed_minb = 2;
-    } else {
-      return fail(CMCG_ERR_INVALID_ARG);
-    }
-  } else {
-    rc = h->prec == CMCG_FP32 ? autotune<float>(h, STAGE_VARIANTS_F32) : autotune<double>(h, 1);
-    if (rc) return fail(rc);
-  }
-  h->launches = 0;
-  *out = h;
-  return CMCG_OK;
+int cmcg_create_batch(int nprob, const cmcg_problem* probs, const cmcg_options* opt, cmcg_handle** out) {
+  return create_impl(nprob, probs, opt, out);
 }
 
 void cmcg_destroy(cmcg_handle* h) {
@@ -784,11 +942,21 @@ int cmcg_set_stream(cmcg_handle* h, void* stream) {
 
 int cmcg_get_sizes(const cmcg_handle* h, int64_t* nt, int* np, int* steps, double* dt, int64_t* field_len) {
   if (!h) return CMCG_ERR_INVALID_ARG;
-  if (nt) *nt = h->nt;
+  if (nt) *nt = h->P[0].nt;
   if (np) *np = h->np;
-  if (steps) *steps = h->M;
-  if (dt) *dt = h->dt;
-  if (field_len) *field_len = h->nt * 6 * h->np;
+  if (steps) *steps = h->P[0].M;
+  if (dt) *dt = h->P[0].dt;
+  if (field_len) *field_len = h->P[0].nt * 6 * h->np;
+  return CMCG_OK;
+}
+
+int cmcg_batch_size(const cmcg_handle* h) { return h ? h->nprob : 0; }
+
+int cmcg_get_problem(const cmcg_handle* h, int p, int64_t* nt, int* steps, double* dt) {
+  if (!h || p < 0 || p >= h->nprob) return CMCG_ERR_INVALID_ARG;
+  if (nt) *nt = h->P[p].nt;
+  if (steps) *steps = h->P[p].M;
+  if (dt) *dt = h->P[p].dt;
   return CMCG_OK;
 }
 
@@ -828,9 +996,9 @@ int cmcg_profile_read(cmcg_handle* h, double* free_ms, int64_t* free_stages, dou
 
 int dgtd_apply(cmcg_handle* h, double t, const double* u, const double* j_re, const double* j_im, int adjoint,
                double* out) {
-  if (!h || !u || !out) return CMCG_ERR_INVALID_ARG;
+  if (!single(h) || !u || !out) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t n = size_t(h->nt) * 6 * h->np, nj = size_t(h->nt) * 3 * h->np;
+  const size_t n = size_t(h->nt_total) * 6 * h->np, nj = size_t(h->nt_total) * 3 * h->np;
   CK(cudaMemcpyAsync(h->ext0, u, n * 8, cudaMemcpyHostToDevice, h->stream));
   if (j_re) CK(cudaMemcpyAsync(h->ext2, j_re, nj * 8, cudaMemcpyHostToDevice, h->stream));
   if (j_re && j_im) CK(cudaMemcpyAsync(h->ext3, j_im, nj * 8, cudaMemcpyHostToDevice, h->stream));
@@ -846,24 +1014,24 @@ int dgtd_apply(cmcg_handle* h, double t, const double* u, const double* j_re, co
 
 int dgtd_period_forward_device(cmcg_handle* h, const double* u0, const double* j_re, const double* j_im, double* uT,
                                double* filt_re, double* filt_im) {
-  if (!h || !u0) return CMCG_ERR_INVALID_ARG;
+  if (!single(h) || !u0) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
   return DISPATCH(h, forward_dev<float>(h, u0, j_re, j_im, uT, filt_re, filt_im),
                   forward_dev<double>(h, u0, j_re, j_im, uT, filt_re, filt_im));
 }
 
 int dgtd_period_adjoint_device(cmcg_handle* h, const double* wT, double* w0) {
-  if (!h || !wT || !w0) return CMCG_ERR_INVALID_ARG;
+  if (!single(h) || !wT || !w0) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
   return DISPATCH(h, adjoint_dev<float>(h, wT, w0), adjoint_dev<double>(h, wT, w0));
 }
 
 int dgtd_period_forward(cmcg_handle* h, const double* u0, const double* j_re, const double* j_im, double* uT,
                         double* filt_re, double* filt_im) {
-  if (!h || !u0) return CMCG_ERR_INVALID_ARG;
+  if (!single(h) || !u0) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t n = size_t(h->nt) * 6 * h->np, nj = size_t(h->nt) * 3 * h->np;
-  // ext0: u0 / uT, ext1: filter re, ext2: filter im, ext3: j (re then im share ext3 halves)
+  const size_t n = size_t(h->nt_total) * 6 * h->np, nj = size_t(h->nt_total) * 3 * h->np;
+  // ext0: u0 / uT, ext1: filter re, ext2: filter im, ext3: j (re, then im)
   CK(cudaMemcpyAsync(h->ext0, u0, n * 8, cudaMemcpyHostToDevice, h->stream));
   const double* jr = nullptr;
   const double* ji = nullptr;
@@ -876,8 +1044,9 @@ int dgtd_period_forward(cmcg_handle* h, const double* u0, const double* j_re, co
     }
   }
   const bool filter = filt_re && filt_im;
-  int rc = DISPATCH(h, forward_dev<float>(h, h->ext0, jr, ji, h->ext0, filter ? h->ext1 : nullptr, filter ? h->ext2 : nullptr),
-                    forward_dev<double>(h, h->ext0, jr, ji, h->ext0, filter ? h->ext1 : nullptr, filter ? h->ext2 : nullptr));
+  int rc = DISPATCH(
+      h, forward_dev<float>(h, h->ext0, jr, ji, h->ext0, filter ? h->ext1 : nullptr, filter ? h->ext2 : nullptr),
+      forward_dev<double>(h, h->ext0, jr, ji, h->ext0, filter ? h->ext1 : nullptr, filter ? h->ext2 : nullptr));
   if (rc) return rc;
   if (uT) CK(cudaMemcpyAsync(uT, h->ext0, n * 8, cudaMemcpyDeviceToHost, h->stream));
   if (filter) {
@@ -889,9 +1058,9 @@ int dgtd_period_forward(cmcg_handle* h, const double* u0, const double* j_re, co
 }
 
 int dgtd_period_adjoint(cmcg_handle* h, const double* wT, double* w0) {
-  if (!h || !wT || !w0) return CMCG_ERR_INVALID_ARG;
+  if (!single(h) || !wT || !w0) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t n = size_t(h->nt) * 6 * h->np;
+  const size_t n = size_t(h->nt_total) * 6 * h->np;
   CK(cudaMemcpyAsync(h->ext0, wT, n * 8, cudaMemcpyHostToDevice, h->stream));
   int rc = DISPATCH(h, adjoint_dev<float>(h, h->ext0, h->ext0), adjoint_dev<double>(h, h->ext0, h->ext0));
   if (rc) return rc;
@@ -901,43 +1070,75 @@ int dgtd_period_adjoint(cmcg_handle* h, const double* wT, double* w0) {
 }
 
 int cmcg_inner(cmcg_handle* h, const double* u, const double* v, double* out) {
-  if (!h || !u || !v || !out) return CMCG_ERR_INVALID_ARG;
+  if (!single(h) || !u || !v || !out) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t n = size_t(h->nt) * 6 * h->np;
+  const size_t n = size_t(h->nt_total) * 6 * h->np;
   CK(cudaMemcpyAsync(h->ext0, u, n * 8, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->ext1, v, n * 8, cudaMemcpyHostToDevice, h->stream));
   return DISPATCH(h, inner_dev<float>(h, h->ext0, h->ext1, out), inner_dev<double>(h, h->ext0, h->ext1, out));
 }
 
-int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
-                      double* e_im, double* h_re, double* h_im, cmcg_info* info) {
+int cmcg_solve_batch_device(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol,
+                            int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
+                            double* const* h_im, cmcg_info* info) {
   if (!h || !j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0) return CMCG_ERR_INVALID_ARG;
+  for (int p = 0; p < h->nprob; ++p)
+    if (!j_re[p] || !e_re[p] || !e_im[p] || !h_re[p] || !h_im[p]) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
   return DISPATCH(h, solve_dev<float>(h, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info),
                   solve_dev<double>(h, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info));
 }
 
-int cmcg_solve(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
-               double* e_im, double* h_re, double* h_im, cmcg_info* info) {
+int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol, int max_iter,
+                     double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im,
+                     cmcg_info* info) {
   if (!h || !j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0) return CMCG_ERR_INVALID_ARG;
+  for (int p = 0; p < h->nprob; ++p)
+    if (!j_re[p] || !e_re[p] || !e_im[p] || !h_re[p] || !h_im[p]) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t nj = size_t(h->nt) * 3 * h->np;
-  // ext3 holds j (re, im); results go to ext0 (e_re, e_im halves) and ext1 (h_re, h_im halves)
-  CK(cudaMemcpyAsync(h->ext3, j_re, nj * 8, cudaMemcpyHostToDevice, h->stream));
-  const double* ji = nullptr;
-  if (j_im) {
-    CK(cudaMemcpyAsync(h->ext3 + nj, j_im, nj * 8, cudaMemcpyHostToDevice, h->stream));
-    ji = h->ext3 + nj;
+  // Staging: ext3 holds j (all re parts, then all im parts), ext0 e and ext1 h (re, then im).
+  const size_t half = size_t(h->nt_total) * 3 * h->np;
+  std::vector<const double*> jr(h->nprob), ji(h->nprob);
+  std::vector<double*> er(h->nprob), ei(h->nprob), hr(h->nprob), hi(h->nprob);
+  for (int p = 0; p < h->nprob; ++p) {
+    const size_t off = size_t(h->P[p].ext0) * 3 * h->np, n = size_t(h->P[p].nt) * 3 * h->np;
+    CK(cudaMemcpyAsync(h->ext3 + off, j_re[p], n * 8, cudaMemcpyHostToDevice, h->stream));
+    jr[p] = h->ext3 + off;
+    ji[p] = nullptr;
+    if (j_im && j_im[p]) {
+      CK(cudaMemcpyAsync(h->ext3 + half + off, j_im[p], n * 8, cudaMemcpyHostToDevice, h->stream));
+      ji[p] = h->ext3 + half + off;
+    }
+    er[p] = h->ext0 + off;
+    ei[p] = h->ext0 + half + off;
+    hr[p] = h->ext1 + off;
+    hi[p] = h->ext1 + half + off;
   }
-  int rc = DISPATCH(h, solve_dev<float>(h, h->ext3, ji, tol, max_iter, h->ext0, h->ext0 + nj, h->ext1, h->ext1 + nj, info),
-                    solve_dev<double>(h, h->ext3, ji, tol, max_iter, h->ext0, h->ext0 + nj, h->ext1, h->ext1 + nj, info));
+  int rc = DISPATCH(
+      h, solve_dev<float>(h, jr.data(), ji.data(), tol, max_iter, er.data(), ei.data(), hr.data(), hi.data(), info),
+      solve_dev<double>(h, jr.data(), ji.data(), tol, max_iter, er.data(), ei.data(), hr.data(), hi.data(), info));
   if (rc < 0) return rc;
-  CK(cudaMemcpyAsync(e_re, h->ext0, nj * 8, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(e_im, h->ext0 + nj, nj * 8, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(h_re, h->ext1, nj * 8, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(h_im, h->ext1 + nj, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+  for (int p = 0; p < h->nprob; ++p) {
+    const size_t n = size_t(h->P[p].nt) * 3 * h->np;
+    CK(cudaMemcpyAsync(e_re[p], er[p], n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(e_im[p], ei[p], n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h_re[p], hr[p], n * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h_im[p], hi[p], n * 8, cudaMemcpyDeviceToHost, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   return rc;
+}
+
+int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
+                      double* e_im, double* h_re, double* h_im, cmcg_info* info) {
+  if (!single(h)) return CMCG_ERR_INVALID_ARG;
+  return cmcg_solve_batch_device(h, &j_re, &j_im, tol, max_iter, &e_re, &e_im, &h_re, &h_im, info);
+}
+
+int cmcg_solve(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
+               double* e_im, double* h_re, double* h_im, cmcg_info* info) {
+  if (!single(h)) return CMCG_ERR_INVALID_ARG;
+  return cmcg_solve_batch(h, &j_re, &j_im, tol, max_iter, &e_re, &e_im, &h_re, &h_im, info);
 }
 
 }  // extern "C"

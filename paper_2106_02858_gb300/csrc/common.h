@@ -89,27 +89,35 @@ int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* 
 constexpr int32_t NBR_PEC = -1;
 constexpr int32_t NBR_IMP = -2;
 
-// Arguments of one RK stage over all tetrahedra.
-//   Phi   = src + B_sigma(vin)      (B_sigma = Sigma B Sigma when sH = -1)
+// Per-problem coefficients of one stage launch (a handle holds a batch of
+// problems that advance in lockstep; each reads its own entry).
+//   Phi   = src + B_sigma(vin),  src = s_cos * jre - s_sin * jim   (B_sigma = Sigma B Sigma when sH = -1)
 //   out   = base + c_out Phi        (skipped if out == nullptr)
 //   acc_o = acc_i + c_acc Phi       (skipped if acc_o == nullptr)
 //   F    += fa vin + fb Phi         (complex weights; skipped if fre == nullptr)
+// A problem whose entry has active == 0 leaves everything untouched.
+template <typename R>
+struct StageCoef {
+  R c_out, c_acc, s_cos, s_sin, fa_re, fa_im, fb_re, fb_im;
+  int32_t active, pad;
+};
+
+// Arguments of one RK stage over all tetrahedra of all problems of a handle.
 template <typename R>
 struct StageArgs {
   const R* vin;
   const R* base;
   R* out;
-  R c_out;
   const R* acc_in;
   R* acc_out;
-  R c_acc;
-  const R* jre;  // E-rows source / eps, [tile][3][Np][32]
+  const R* jre;  // E-rows source / eps, [tile][3][Np][32] (null: no source)
   const R* jim;
-  R s_cos, s_sin;  // Re(J e^{iwt}) = jre cos - jim sin
-  R* fre;
+  R* fre;        // filter accumulators (null: no filter)
   R* fim;
-  R fa_re, fa_im, fb_re, fb_im;
-  R sH;  // +1 forward, -1 adjoint
+  R sH;          // +1 forward, -1 adjoint
+  const StageCoef<R>* coef;  // [problem] for this launch
+  const int32_t* tprob;      // problem of each tile (null: every tile is problem 0)
+  const int32_t* pactive;    // per-problem CG activity (null: all active)
   const R* gvol;
   const R* gface;
   const int32_t* nbr;
@@ -132,8 +140,21 @@ void launch_stage_packed(const StageArgs<float>& a, cudaStream_t s, int minb);
 struct Scalars {
   double rr, rr_new, dA, alpha, beta, rr0;
   int status;
-  int pad;
+  int iters;
 };
+
+// Blocks of the problem-aligned reductions: block b covers internal tets
+// [tet0[b], tet0[b] + ntet[b]) of problem prob[b]; problem p owns blocks
+// [pb0[p], pb0[p + 1]).
+struct BlockTable {
+  const int64_t* tet0;
+  const int32_t* ntet;
+  const int32_t* prob;
+  const int32_t* pb0;
+  int nblk;
+  int nprob;
+};
+constexpr int DOT_THREADS = 128;
 
 // Layout conversion over (tet, c in [0, cnt), node):
 //   internal [tile][ncomp_in][np][32] at component c_in0 + c  <->  external [tet][ncomp_ext][np] at c_ext0 + c.
@@ -149,21 +170,28 @@ void launch_to_external(const R* in, int ncomp_in, int c_in0, double* ext, int n
 template <typename R>
 void launch_lincomb3(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n, cudaStream_t s);
 
-// M-weighted dot products and CG updates (vec.cu); Q-dispatched internally.
+// (eps, mu)-weighted dots and CG updates, one partial per block of the table.
 template <typename R>
 void launch_cg_after_adjoint(int q, const R* Uw, const R* WT, R* A, const R* D, const double* wdot, double* partials,
-                             int64_t nti, cudaStream_t s);
+                             const BlockTable& bt, const int32_t* pactive, cudaStream_t s);
 template <typename R>
 void launch_cg_update(int q, R* U0, R* Rv, const R* D, const R* A, const double* wdot, const Scalars* sc,
-                      double* partials, int64_t nti, cudaStream_t s);
+                      double* partials, const BlockTable& bt, const int32_t* pactive, cudaStream_t s);
 template <typename R>
-void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* partials, int64_t nti, cudaStream_t s);
+void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* partials, const BlockTable& bt,
+                cudaStream_t s);
+// D = R + beta_p D and Uw = D on the tiles of active problems.
 template <typename R>
-void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, int64_t n, cudaStream_t s);
-
-int dot_blocks(int64_t nti);
-// which: 0 -> rr (and rr0), 1 -> dA (then alpha = rr / dA), 2 -> rr_new (then beta), 3 -> generic into rr_new
-void launch_finalize(double* partials, int nblocks, Scalars* sc, int which, cudaStream_t s);
+void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob, const int32_t* pactive,
+                         int64_t n, int np, cudaStream_t s);
+// One block per problem sums its partials in a fixed order.
+//   which 0: rr = rr0 = total, active = (rr0 > 0 and tol < 1)
+//   which 1: dA = total, alpha = rr / dA (breakdown if dA <= 0)
+//   which 2: beta = total / rr, rr = total, iters += 1, active = (sqrt(rr) > tol sqrt(rr0))
+//   which 3: rr_new = total
+// Problems with pactive[p] == 0 are left alone for which 1 and 2.
+void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, int32_t* pactive, int which, double tol,
+                     cudaStream_t s);
 void upload_dot_mass(int q, const double* M);
 
 // Gauss-Legendre rule on [0, 1] (refelem.cpp).

@@ -94,6 +94,11 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
   const int half = int(gthr & 1);  // 0: owns E, computes Phi_H;  1: owns H, computes Phi_E
   const int64_t tile = gt >> 5;
   const int lane = int(gt & 31);
+  // A warp (16 tetrahedra) lies inside one tile, hence inside one problem: uniform exits.
+  const int prob = a.tprob ? a.tprob[tile] : 0;
+  if (a.pactive && !a.pactive[prob]) return;
+  const StageCoef<R> cf = a.coef[prob];
+  if (!cf.active) return;
   const int cOwn = half ? 3 : 0, cOut = half ? 0 : 3;
   const R sH = a.sH;
   const R sIn = half ? sH : R(1);   // sign of the own field (magnetic values flipped in the adjoint)
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
 #pragma unroll
       for (int n = 0; n < NP; ++n) {
         const int64_t o = joff + (c * NP + n) * TILE;
-        phi[c][n] += a.s_cos * a.jre[o] - a.s_sin * a.jim[o];
+        phi[c][n] += cf.s_cos * a.jre[o] - cf.s_sin * a.jim[o];
       }
   }
   if (a.fre) {  // forward sweeps only: F += fa U + fb Phi on this thread's output rows
@@ -237,8 +242,8 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
       for (int n = 0; n < NP; ++n) {
         const int64_t o = off + (c * NP + n) * TILE;
         const R u = a.vin[o];
-        a.fre[o] += a.fa_re * u + a.fb_re * phi[c][n];
-        a.fim[o] += a.fa_im * u + a.fb_im * phi[c][n];
+        a.fre[o] += cf.fa_re * u + cf.fb_re * phi[c][n];
+        a.fim[o] += cf.fa_im * u + cf.fb_im * phi[c][n];
       }
   }
   if (a.acc_out) {
@@ -247,7 +252,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
 #pragma unroll
       for (int n = 0; n < NP; ++n) {
         const int64_t o = off + (c * NP + n) * TILE;
-        a.acc_out[o] = a.acc_in[o] + a.c_acc * phi[c][n];
+        a.acc_out[o] = a.acc_in[o] + cf.c_acc * phi[c][n];
       }
   }
   if (a.out) {
@@ -256,7 +261,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
 #pragma unroll
       for (int n = 0; n < NP; ++n) {
         const int64_t o = off + (c * NP + n) * TILE;
-        a.out[o] = bv[c][n] + a.c_out * phi[c][n];
+        a.out[o] = bv[c][n] + cf.c_out * phi[c][n];
       }
   }
 }
@@ -291,6 +296,10 @@ __global__ void __launch_bounds__(PK_THREADS, MINB) dg_stage_packed(const StageA
   constexpr FaceTab FM = make_fmask(CMCG_Q);
   const int64_t tile = (int64_t(blockIdx.x) * PK_THREADS + threadIdx.x) >> 5;
   if (tile * TILE >= a.nti) return;
+  const int prob = a.tprob ? a.tprob[tile] : 0;
+  if (a.pactive && !a.pactive[prob]) return;
+  const StageCoef<float> cf = a.coef[prob];
+  if (!cf.active) return;
   const int lane = threadIdx.x & 31;
   const int half = lane & 1;
   const int t0 = (lane >> 1) * 2;  // first of the lane's two tetrahedra within the tile
@@ -422,7 +431,7 @@ __global__ void __launch_bounds__(PK_THREADS, MINB) dg_stage_packed(const StageA
 
   if (half && a.jre) {
     const int64_t joff = tile * (3 * NP * TILE) + t0;
-    const float2 sc = f2(a.s_cos), ss = f2(-a.s_sin);
+    const float2 sc = f2(cf.s_cos), ss = f2(-cf.s_sin);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -433,7 +442,7 @@ __global__ void __launch_bounds__(PK_THREADS, MINB) dg_stage_packed(const StageA
       }
   }
   if (a.fre) {
-    const float2 far = f2(a.fa_re), fai = f2(a.fa_im), fbr = f2(a.fb_re), fbi = f2(a.fb_im);
+    const float2 far = f2(cf.fa_re), fai = f2(cf.fa_im), fbr = f2(cf.fb_re), fbi = f2(cf.fb_im);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -447,7 +456,7 @@ __global__ void __launch_bounds__(PK_THREADS, MINB) dg_stage_packed(const StageA
       }
   }
   if (a.acc_out) {
-    const float2 ca = f2(a.c_acc);
+    const float2 ca = f2(cf.c_acc);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -457,7 +466,7 @@ __global__ void __launch_bounds__(PK_THREADS, MINB) dg_stage_packed(const StageA
       }
   }
   if (a.out) {
-    const float2 co = f2(a.c_out);
+    const float2 co = f2(cf.c_out);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll

@@ -12,8 +12,6 @@
 namespace cmcg {
 namespace {
 
-constexpr int DOT_THREADS = 128;
-constexpr int DOT_MAX_BLOCKS = 4096;
 
 __constant__ double cM1[4 * 4];
 __constant__ double cM2[10 * 10];
@@ -117,32 +115,45 @@ __device__ __forceinline__ double tet_dot(const R* X, const R* Y, int64_t tile, 
   return total;
 }
 
+// Block b of the table: its tets, or -1 when past the block's range.
+__device__ __forceinline__ int64_t block_tet(const BlockTable& bt) {
+  const int b = blockIdx.x;
+  return threadIdx.x < bt.ntet[b] ? bt.tet0[b] + threadIdx.x : -1;
+}
+
 // A = Uw - WT; partial (D, A).
 template <int Q, typename R>
 __global__ void __launch_bounds__(DOT_THREADS) cg_after_adjoint_kernel(const R* Uw, const R* WT, R* A, const R* D,
-                                                                      const double* wdot, double* partials, int64_t nti) {
+                                                                      const double* wdot, double* partials,
+                                                                      const BlockTable bt, const int32_t* pactive) {
   constexpr int NP = np_of(Q);
+  const bool act = !pactive || pactive[bt.prob[blockIdx.x]];
+  const int64_t t = block_tet(bt);
   double acc = 0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nti; t += (int64_t)gridDim.x * blockDim.x) {
+  if (act && t >= 0) {
     const int64_t tile = t >> 5;
     const int lane = int(t & 31);
     const int64_t base = tile * (6 * NP * TILE) + lane;
 #pragma unroll
     for (int k = 0; k < 6 * NP; ++k) A[base + k * TILE] = R(double(Uw[base + k * TILE]) - double(WT[base + k * TILE]));
-    acc += tet_dot<Q, R>(D, A, tile, lane, wdot);
+    acc = tet_dot<Q, R>(D, A, tile, lane, wdot);
   }
   const double s = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// U0 += alpha D; R -= alpha A; partial (R, R).
+// U0 += alpha_p D; R -= alpha_p A; partial (R, R).
 template <int Q, typename R>
 __global__ void __launch_bounds__(DOT_THREADS) cg_update_kernel(R* U0, R* Rv, const R* D, const R* A, const double* wdot,
-                                                               const Scalars* sc, double* partials, int64_t nti) {
+                                                               const Scalars* sc, double* partials, const BlockTable bt,
+                                                               const int32_t* pactive) {
   constexpr int NP = np_of(Q);
-  const double alpha = sc->alpha;
+  const int p = bt.prob[blockIdx.x];
+  const bool act = !pactive || pactive[p];
+  const int64_t t = block_tet(bt);
   double acc = 0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nti; t += (int64_t)gridDim.x * blockDim.x) {
+  if (act && t >= 0) {
+    const double alpha = sc[p].alpha;
     const int64_t tile = t >> 5;
     const int lane = int(t & 31);
     const int64_t base = tile * (6 * NP * TILE) + lane;
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(DOT_THREADS) cg_update_kernel(R* U0, R* Rv, co
       U0[o] = R(double(U0[o]) + alpha * double(D[o]));
       Rv[o] = R(double(Rv[o]) - alpha * double(A[o]));
     }
-    acc += tet_dot<Q, R>(Rv, Rv, tile, lane, wdot);
+    acc = tet_dot<Q, R>(Rv, Rv, tile, lane, wdot);
   }
   const double s = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -160,56 +171,75 @@ __global__ void __launch_bounds__(DOT_THREADS) cg_update_kernel(R* U0, R* Rv, co
 
 template <int Q, typename R>
 __global__ void __launch_bounds__(DOT_THREADS) dot_kernel(const R* X, const R* Y, const double* wdot, double* partials,
-                                                         int64_t nti) {
-  double acc = 0;
-  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nti; t += (int64_t)gridDim.x * blockDim.x)
-    acc += tet_dot<Q, R>(X, Y, t >> 5, int(t & 31), wdot);
+                                                         const BlockTable bt) {
+  const int64_t t = block_tet(bt);
+  const double acc = t >= 0 ? tet_dot<Q, R>(X, Y, t >> 5, int(t & 31), wdot) : 0.0;
   const double s = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// D = R + beta D; Uw = D.
+// D = R + beta_p D; Uw = D (active problems only).
 template <typename R>
-__global__ void cg_direction_kernel(R* D, R* Uw, const R* Rv, const Scalars* sc, int64_t n) {
-  const double beta = sc->beta;
+__global__ void cg_direction_kernel(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob,
+                                    const int32_t* pactive, int64_t n, int64_t tile_len) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const R v = R(double(Rv[i]) + beta * double(D[i]));
+    const int p = tprob ? tprob[i / tile_len] : 0;
+    if (pactive && !pactive[p]) continue;
+    const R v = R(double(Rv[i]) + sc[p].beta * double(D[i]));
     D[i] = v;
     Uw[i] = v;
   }
 }
 
-__global__ void finalize_kernel(const double* partials, int nblocks, Scalars* sc, int which) {
+__global__ void finalize_kernel(const double* partials, const BlockTable bt, Scalars* sc, int32_t* pactive, int which,
+                                double tol) {
   __shared__ double sh[256];
+  const int p = blockIdx.x;
+  const int b0 = bt.pb0[p], b1 = bt.pb0[p + 1];
   double s = 0;
-  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) s += partials[i];
+  for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += partials[i];
   sh[threadIdx.x] = s;
   __syncthreads();
   for (int w = 128; w > 0; w >>= 1) {
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const double tot = sh[0];
-    if (!isfinite(tot)) sc->status = CMCG_ERR_NONFINITE;
-    if (which == 0) {
-      sc->rr = tot;
-      sc->rr0 = tot;
-    } else if (which == 1) {
-      sc->dA = tot;
-      if (!(tot > 0)) {
-        if (sc->status == 0) sc->status = CMCG_ERR_CG_BREAKDOWN;
-        sc->alpha = 0;
-      } else {
-        sc->alpha = sc->rr / tot;
-      }
-    } else if (which == 2) {
-      sc->rr_new = tot;
-      sc->beta = sc->rr > 0 ? tot / sc->rr : 0.0;
-      sc->rr = tot;
+  if (threadIdx.x != 0) return;
+  const double tot = sh[0];
+  Scalars& S = sc[p];
+  if (which == 3) {
+    S.rr_new = tot;
+    return;
+  }
+  if (which == 0) {
+    S.rr = tot;
+    S.rr0 = tot;
+    S.iters = 0;
+    S.status = isfinite(tot) ? 0 : CMCG_ERR_NONFINITE;
+    if (pactive) pactive[p] = (S.status == 0 && tot > 0 && sqrt(tot) > tol * sqrt(tot)) ? 1 : 0;
+    return;
+  }
+  if (pactive && !pactive[p]) return;
+  if (!isfinite(tot)) {
+    S.status = CMCG_ERR_NONFINITE;
+    if (pactive) pactive[p] = 0;
+    return;
+  }
+  if (which == 1) {
+    S.dA = tot;
+    if (!(tot > 0)) {
+      S.status = CMCG_ERR_CG_BREAKDOWN;
+      S.alpha = 0;
+      if (pactive) pactive[p] = 0;
     } else {
-      sc->rr_new = tot;
+      S.alpha = S.rr / tot;
     }
+  } else {  // which == 2
+    S.rr_new = tot;
+    S.beta = S.rr > 0 ? tot / S.rr : 0.0;
+    S.rr = tot;
+    S.iters += 1;
+    if (pactive && !(sqrt(tot) > tol * sqrt(S.rr0))) pactive[p] = 0;
   }
 }
 
@@ -221,13 +251,6 @@ int grid_for(int64_t n, int threads) {
 }
 
 }  // namespace
-
-int dot_blocks(int64_t nti) {
-  int64_t b = (nti + DOT_THREADS - 1) / DOT_THREADS;
-  if (b > DOT_MAX_BLOCKS) b = DOT_MAX_BLOCKS;
-  if (b < 1) b = 1;
-  return int(b);
-}
 
 void upload_dot_mass(int q, const double* M) {
   const int np = np_of(q);
@@ -255,36 +278,36 @@ void launch_lincomb3(R* o1, R* o2, R* o3, double a, const R* x, double b, const 
   lincomb_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(o1, o2, o3, a, x, b, y, n);
 }
 
-#define CMCG_DISPATCH_Q(q, KERNEL, ...)                                       \
-  do {                                                                        \
-    if ((q) == 1) KERNEL<1, R><<<nb, DOT_THREADS, 0, s>>>(__VA_ARGS__);       \
-    else if ((q) == 2) KERNEL<2, R><<<nb, DOT_THREADS, 0, s>>>(__VA_ARGS__);  \
-    else KERNEL<3, R><<<nb, DOT_THREADS, 0, s>>>(__VA_ARGS__);                \
+#define CMCG_DISPATCH_Q(q, KERNEL, ...)                                             \
+  do {                                                                              \
+    if ((q) == 1) KERNEL<1, R><<<bt.nblk, DOT_THREADS, 0, s>>>(__VA_ARGS__);        \
+    else if ((q) == 2) KERNEL<2, R><<<bt.nblk, DOT_THREADS, 0, s>>>(__VA_ARGS__);   \
+    else KERNEL<3, R><<<bt.nblk, DOT_THREADS, 0, s>>>(__VA_ARGS__);                 \
   } while (0)
 
 template <typename R>
 void launch_cg_after_adjoint(int q, const R* Uw, const R* WT, R* A, const R* D, const double* wdot, double* partials,
-                             int64_t nti, cudaStream_t s) {
-  const int nb = dot_blocks(nti);
-  CMCG_DISPATCH_Q(q, cg_after_adjoint_kernel, Uw, WT, A, D, wdot, partials, nti);
+                             const BlockTable& bt, const int32_t* pactive, cudaStream_t s) {
+  CMCG_DISPATCH_Q(q, cg_after_adjoint_kernel, Uw, WT, A, D, wdot, partials, bt, pactive);
 }
 template <typename R>
 void launch_cg_update(int q, R* U0, R* Rv, const R* D, const R* A, const double* wdot, const Scalars* sc,
-                      double* partials, int64_t nti, cudaStream_t s) {
-  const int nb = dot_blocks(nti);
-  CMCG_DISPATCH_Q(q, cg_update_kernel, U0, Rv, D, A, wdot, sc, partials, nti);
+                      double* partials, const BlockTable& bt, const int32_t* pactive, cudaStream_t s) {
+  CMCG_DISPATCH_Q(q, cg_update_kernel, U0, Rv, D, A, wdot, sc, partials, bt, pactive);
 }
 template <typename R>
-void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* partials, int64_t nti, cudaStream_t s) {
-  const int nb = dot_blocks(nti);
-  CMCG_DISPATCH_Q(q, dot_kernel, X, Y, wdot, partials, nti);
+void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* partials, const BlockTable& bt,
+                cudaStream_t s) {
+  CMCG_DISPATCH_Q(q, dot_kernel, X, Y, wdot, partials, bt);
 }
 template <typename R>
-void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, int64_t n, cudaStream_t s) {
-  cg_direction_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(D, Uw, Rv, sc, n);
+void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob, const int32_t* pactive,
+                         int64_t n, int np, cudaStream_t s) {
+  cg_direction_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(D, Uw, Rv, sc, tprob, pactive, n, int64_t(6) * np * TILE);
 }
-void launch_finalize(double* partials, int nblocks, Scalars* sc, int which, cudaStream_t s) {
-  finalize_kernel<<<1, 256, 0, s>>>(partials, nblocks, sc, which);
+void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, int32_t* pactive, int which, double tol,
+                     cudaStream_t s) {
+  finalize_kernel<<<bt.nprob, 256, 0, s>>>(partials, bt, sc, pactive, which, tol);
 }
 
 #define CMCG_INST(R)                                                                                                  \
@@ -293,12 +316,13 @@ void launch_finalize(double* partials, int nblocks, Scalars* sc, int which, cuda
   template void launch_to_external<R>(const R*, int, int, double*, int, int, int, const int32_t*, int64_t, int,       \
                                       cudaStream_t);                                                                  \
   template void launch_lincomb3<R>(R*, R*, R*, double, const R*, double, const R*, int64_t, cudaStream_t);             \
-  template void launch_cg_after_adjoint<R>(int, const R*, const R*, R*, const R*, const double*, double*, int64_t,     \
-                                           cudaStream_t);                                                             \
-  template void launch_cg_update<R>(int, R*, R*, const R*, const R*, const double*, const Scalars*, double*, int64_t, \
-                                    cudaStream_t);                                                                    \
-  template void launch_dot<R>(int, const R*, const R*, const double*, double*, int64_t, cudaStream_t);               \
-  template void launch_cg_direction<R>(R*, R*, const R*, const Scalars*, int64_t, cudaStream_t);
+  template void launch_cg_after_adjoint<R>(int, const R*, const R*, R*, const R*, const double*, double*,              \
+                                           const BlockTable&, const int32_t*, cudaStream_t);                          \
+  template void launch_cg_update<R>(int, R*, R*, const R*, const R*, const double*, const Scalars*, double*,          \
+                                    const BlockTable&, const int32_t*, cudaStream_t);                                 \
+  template void launch_dot<R>(int, const R*, const R*, const double*, double*, const BlockTable&, cudaStream_t);      \
+  template void launch_cg_direction<R>(R*, R*, const R*, const Scalars*, const int32_t*, const int32_t*, int64_t,     \
+                                       int, cudaStream_t);
 CMCG_INST(float)
 CMCG_INST(double)
 
