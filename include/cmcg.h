@@ -59,6 +59,7 @@ extern "C" {
 enum cmcg_status {
   CMCG_OK = 0,
   CMCG_NOT_CONVERGED = 1,
+  CMCG_PENDING = 2,
   CMCG_ERR_INVALID_ARG = -1,
   CMCG_ERR_NONCONFORMING_MESH = -2,
   CMCG_ERR_OUT_OF_MEMORY = -3,
@@ -271,6 +272,18 @@ int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* co
                      double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im,
                      cmcg_info* info);
 
+/* cmcg_solve_batch restricted to problems [0, n) of the handle (1 <= n <= nprob):
+ * the other problems are skipped by every kernel, so one handle built for a
+ * capacity of n_max requests can serve any smaller group.  Arrays hold n host
+ * pointers. */
+int cmcg_solve_batch_n(cmcg_handle* h, int n, const double* const* j_re, const double* const* j_im, double tol,
+                       int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
+                       double* const* h_im, cmcg_info* info);
+
+/* Device memory held by a handle, in bytes (the figure cmcg_create checks
+ * against hbm_budget_bytes). */
+int64_t cmcg_device_bytes(const cmcg_handle* h);
+
 /* Device-pointer form of cmcg_solve_batch (the pointer arrays live on the host). */
 int cmcg_solve_batch_device(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol,
                             int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
@@ -295,6 +308,61 @@ int64_t cmcg_kernel_launches(const cmcg_handle* h);
 int cmcg_profile_enable(cmcg_handle* h, int on);
 int cmcg_profile_read(cmcg_handle* h, double* free_ms, int64_t* free_stages, double* source_ms,
                       int64_t* source_stages);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of CMCG requests (no counterpart in the paper;
+ * it serves many independent solves of the paper's method).
+ *
+ * A server holds registered models (mesh, eps, mu, omega, order) and a queue
+ * of requests (one source each).  Worker threads, each with its own CUDA
+ * stream, take the oldest request, gather up to the model's batch capacity of
+ * queued requests of the same model (waiting at most max_wait_ms), and solve
+ * them together (cmcg_solve_batch_n) on a pooled batch handle; batches of
+ * different workers run concurrently.  New handles are created only while the
+ * server's device memory stays within hbm_budget_bytes (0 = no limit);
+ * otherwise a batch waits for a pooled handle.  Every handle of a model uses
+ * the kernel form chosen when the model was registered, so a request's result
+ * is the one it gets when solved alone, whatever shares its batch. */
+typedef struct cmcg_server cmcg_server;
+
+typedef struct cmcg_server_options {
+  int device;
+  int precision;      /* CMCG_FP32 (default) or CMCG_FP64 */
+  int max_batch;      /* default batch capacity per model (default 8) */
+  int workers;        /* worker threads / streams (default 2) */
+  double max_wait_ms; /* micro-batching window (default 2) */
+  double tol;         /* CG tolerance of every request (default 1e-6) */
+  int max_iter;       /* default 1000 */
+  int64_t hbm_budget_bytes;
+  int stage_variant;  /* 0: choose per model by timing; k > 0: as cmcg_options.stage_variant */
+  int reserved[7];
+} cmcg_server_options;
+
+void cmcg_server_default_options(cmcg_server_options* opt);
+int cmcg_server_create(const cmcg_server_options* opt, cmcg_server** out);
+
+/* Registers a model (copied) with batch capacity max_batch (0 = server
+ * default); builds its first handle.  *model receives its id. */
+int cmcg_server_add_model(cmcg_server* s, const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
+                          int order, int max_batch, int* model);
+
+/* Queues one request (j_re, j_im: double[nt][3][Np], copied; j_im may be
+ * NULL).  *ticket identifies it. */
+int cmcg_server_submit(cmcg_server* s, int model, const double* j_re, const double* j_im, int64_t* ticket);
+
+/* Result of a request.  wait == 0: returns CMCG_PENDING while it is queued or
+ * running.  Otherwise (or once done) copies (e, h) (double[nt][3][Np] each; any
+ * pointer may be NULL), the solve report, and latency_ms[0] = submit to
+ * completion, latency_ms[1] = submit to start (may be NULL), forgets the
+ * ticket and returns the request's status. */
+int cmcg_server_poll(cmcg_server* s, int64_t ticket, int wait, double* e_re, double* e_im, double* h_re,
+                     double* h_im, cmcg_info* info, double* latency_ms);
+
+/* Requests completed, requests queued, device bytes held, handles created. */
+int cmcg_server_stats(cmcg_server* s, int64_t* completed, int64_t* queued, int64_t* bytes_in_use, int* handles);
+
+/* Drains the queue, joins the workers and releases every handle. */
+void cmcg_server_destroy(cmcg_server* s);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,7 @@ _LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libcmcg.so
 
 CMCG_OK = 0
 CMCG_NOT_CONVERGED = 1
+CMCG_PENDING = 2
 CMCG_ERR_INVALID_ARG = -1
 CMCG_ERR_NONCONFORMING_MESH = -2
 CMCG_ERR_OUT_OF_MEMORY = -3
@@ -56,6 +57,12 @@ class cmcg_problem(C.Structure):
                 ("omega", C.c_double)]
 
 
+class cmcg_server_options(C.Structure):
+    _fields_ = [("device", C.c_int), ("precision", C.c_int), ("max_batch", C.c_int), ("workers", C.c_int),
+                ("max_wait_ms", C.c_double), ("tol", C.c_double), ("max_iter", C.c_int),
+                ("hbm_budget_bytes", C.c_int64), ("stage_variant", C.c_int), ("reserved", C.c_int * 7)]
+
+
 class CMCGError(RuntimeError):
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {cmcg_status_string(code)} ({code})")
@@ -87,6 +94,19 @@ def _load() -> C.CDLL:
         "cmcg_solve_batch_device": (C.c_int, [_vp, C.POINTER(_vp), C.POINTER(_vp), C.c_double, C.c_int,
                                               C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(_vp),
                                               C.POINTER(cmcg_info)]),
+        "cmcg_solve_batch_n": (C.c_int, [_vp, C.c_int, C.POINTER(_dp), C.POINTER(_dp), C.c_double, C.c_int,
+                                         C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp),
+                                         C.POINTER(cmcg_info)]),
+        "cmcg_device_bytes": (C.c_int64, [_vp]),
+        "cmcg_server_default_options": (None, [C.POINTER(cmcg_server_options)]),
+        "cmcg_server_create": (C.c_int, [C.POINTER(cmcg_server_options), C.POINTER(_vp)]),
+        "cmcg_server_add_model": (C.c_int, [_vp, C.POINTER(cmcg_mesh), _dp, _dp, C.c_double, C.c_int, C.c_int,
+                                            C.POINTER(C.c_int)]),
+        "cmcg_server_submit": (C.c_int, [_vp, C.c_int, _dp, _dp, C.POINTER(C.c_int64)]),
+        "cmcg_server_poll": (C.c_int, [_vp, C.c_int64, C.c_int, _dp, _dp, _dp, _dp, C.POINTER(cmcg_info), _dp]),
+        "cmcg_server_stats": (C.c_int, [_vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                        C.POINTER(C.c_int)]),
+        "cmcg_server_destroy": (None, [_vp]),
         "cmcg_destroy": (None, [_vp]),
         "cmcg_set_stream": (C.c_int, [_vp, _vp]),
         "cmcg_get_tuning": (C.c_int, [_vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
@@ -120,7 +140,9 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "dgtd_period_adjoint", "dgtd_period_forward_device", "dgtd_period_adjoint_device", "cmcg_solve",
             "cmcg_solve_device", "cmcg_kernel_launches", "cmcg_profile_enable", "cmcg_profile_read",
             "cmcg_inner", "cmcg_inner_noalloc", "cmcg_get_tuning", "cmcg_create_batch", "cmcg_batch_size",
-            "cmcg_get_problem", "cmcg_solve_batch", "cmcg_solve_batch_device")
+            "cmcg_get_problem", "cmcg_solve_batch", "cmcg_solve_batch_device", "cmcg_solve_batch_n",
+            "cmcg_device_bytes", "cmcg_server_default_options", "cmcg_server_create", "cmcg_server_add_model",
+            "cmcg_server_submit", "cmcg_server_poll", "cmcg_server_stats", "cmcg_server_destroy")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
 
@@ -442,3 +464,98 @@ def create_for_problem(problem, precision: int = CMCG_FP64, flux: int = CMCG_FLU
                                steps_per_period=steps_per_period, device=device, hbm_budget_bytes=hbm_budget_bytes,
                                stage_variant=stage_variant)
     return cmcg_create(mesh, problem.eps, problem.mu, problem.omega, opt), mesh
+
+
+def cmcg_solve_batch_n(h: Handle, n: int, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 1000):
+    """Solve problems [0, n) of a batch handle; lists of n (nt_p, 3, Np) sources."""
+    jr = [_f64(j_re[p], (h.problems[p][0], 3, h.np), "j_re") for p in range(n)]
+    ji = [None if (j_im is None or j_im[p] is None) else _f64(j_im[p], (h.problems[p][0], 3, h.np), "j_im")
+          for p in range(n)]
+    outs = [[np.empty((h.problems[p][0], 3, h.np)) for p in range(n)] for _ in range(4)]
+    P = C.POINTER(C.c_double)
+    arr = lambda xs: (P * n)(*[_ptr(x) if x is not None else P() for x in xs])
+    infos = (cmcg_info * n)()
+    rc = _lib.cmcg_solve_batch_n(h.ptr, int(n), arr(jr), arr(ji), float(tol), int(max_iter), arr(outs[0]),
+                                 arr(outs[1]), arr(outs[2]), arr(outs[3]), infos)
+    _check(rc, "cmcg_solve_batch_n", allow_not_converged=True)
+    return ([outs[0][p] + 1j * outs[1][p] for p in range(n)], [outs[2][p] + 1j * outs[3][p] for p in range(n)],
+            list(infos))
+
+
+def cmcg_device_bytes(h: Handle) -> int:
+    return int(_lib.cmcg_device_bytes(h.ptr))
+
+
+def cmcg_server_default_options(**kw) -> cmcg_server_options:
+    o = cmcg_server_options()
+    _lib.cmcg_server_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Server:
+    """Owns a cmcg_server (cmcg_server_create / cmcg_server_destroy)."""
+
+    def __init__(self, opt: cmcg_server_options):
+        out = C.c_void_p()
+        _check(_lib.cmcg_server_create(C.byref(opt), C.byref(out)), "cmcg_server_create")
+        self.ptr = out
+        self.models = {}  # model id -> (nt, Np)
+        self._keep = []
+
+    def close(self):
+        if self.ptr is not None and self.ptr.value:
+            _lib.cmcg_server_destroy(self.ptr)
+        self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def cmcg_server_create(opt: cmcg_server_options) -> Server:
+    return Server(opt)
+
+
+def cmcg_server_add_model(s: Server, mesh: MeshArrays, eps, mu, omega: float, order: int, max_batch: int = 0) -> int:
+    e, m = _f64(eps), _f64(mu)
+    mid = C.c_int()
+    _check(_lib.cmcg_server_add_model(s.ptr, C.byref(mesh.struct), _ptr(e), _ptr(m), float(omega), int(order),
+                                      int(max_batch), C.byref(mid)), "cmcg_server_add_model")
+    s.models[mid.value] = (mesh.tets.shape[0], (order + 1) * (order + 2) * (order + 3) // 6)
+    return mid.value
+
+
+def cmcg_server_submit(s: Server, model: int, j_re, j_im=None) -> int:
+    nt, np_ = s.models[model]
+    jr, ji = _f64(j_re, (nt, 3, np_), "j_re"), _f64(j_im, (nt, 3, np_), "j_im")
+    t = C.c_int64()
+    _check(_lib.cmcg_server_submit(s.ptr, int(model), _ptr(jr), _ptr(ji), C.byref(t)), "cmcg_server_submit")
+    return t.value
+
+
+def cmcg_server_poll(s: Server, ticket: int, model: int, wait: bool = True):
+    """None while pending (wait=False); else (status, e, h, info, latency_ms, queue_ms)."""
+    nt, np_ = s.models[model]
+    er, ei, hr, hi = (np.empty((nt, 3, np_)) for _ in range(4))
+    info = cmcg_info()
+    lat = (C.c_double * 2)()
+    rc = _lib.cmcg_server_poll(s.ptr, int(ticket), int(bool(wait)), _ptr(er), _ptr(ei), _ptr(hr), _ptr(hi),
+                               C.byref(info), lat)
+    if rc == CMCG_PENDING:
+        return None
+    _check(rc, "cmcg_server_poll", allow_not_converged=True)
+    return rc, er + 1j * ei, hr + 1j * hi, info, lat[0], lat[1]
+
+
+def cmcg_server_stats(s: Server):
+    c, q, b, n = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int()
+    _check(_lib.cmcg_server_stats(s.ptr, C.byref(c), C.byref(q), C.byref(b), C.byref(n)), "cmcg_server_stats")
+    return {"completed": c.value, "queued": q.value, "bytes_in_use": b.value, "handles": n.value}
+
+
+def cmcg_server_destroy(s: Server) -> None:
+    s.close()

@@ -74,6 +74,8 @@ struct cmcg_handle {
   Scalars* sc_host = nullptr;  // pinned
   int32_t* pactive = nullptr;
   int32_t* pactive_host = nullptr;  // pinned
+  int32_t* used = nullptr;          // problems taking part in the current solve
+  int32_t* used_host = nullptr;     // pinned
   int64_t* bt_tet0 = nullptr;
   int32_t *bt_ntet = nullptr, *bt_prob = nullptr, *bt_pb0 = nullptr;
   BlockTable bt{};
@@ -337,7 +339,7 @@ void sweep_free(cmcg_handle* h, bool adjoint, const int32_t* pactive) {
 // Sweep with source (Algorithms rk2 / rk4 as printed) of Uw in place; optional
 // on-the-fly filter (one extra launch evaluates Phi at t_M).
 template <typename R>
-void sweep_source(cmcg_handle* h, bool with_source, bool filter) {
+void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* mask = nullptr) {
   cmcg_handle::SweepEv* pe = prof_begin(h, true);
   R* Uw = (R*)h->Uw;
   R* vA = (R*)h->vA;
@@ -372,6 +374,7 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter) {
       a.fim = (R*)h->Fim;
     }
     a.coef = tab<R>(table, l, h->nprob);
+    a.pactive = mask;
     stage<R>(h, a);
   }
   prof_end(h, pe);
@@ -471,8 +474,8 @@ void lincomb(cmcg_handle* h, void* o1, void* o2, void* o3, double a, const void*
 }
 
 template <typename R>
-int set_source(cmcg_handle* h, const double* const* j_re, const double* const* j_im) {
-  for (int p = 0; p < h->nprob; ++p) {
+int set_source(cmcg_handle* h, const double* const* j_re, const double* const* j_im, int nused = -1) {
+  for (int p = 0; p < (nused < 0 ? h->nprob : nused); ++p) {
     to_int<R>(h, p, j_re[p], 3, h->Jre, 3, 3, h->inv_eps);
     const double* ji = j_im ? j_im[p] : nullptr;
     if (ji) {
@@ -558,7 +561,7 @@ int inner_dev(cmcg_handle* h, const double* u, const double* v, double* out) {
   to_int<R>(h, 0, u, 6, h->Uw, 6, 6, nullptr);
   to_int<R>(h, 0, v, 6, h->vA, 6, 6, nullptr);
   launch_dot<R>(h->q, (const R*)h->Uw, (const R*)h->vA, h->wdot, h->partials, h->bt, h->stream);
-  launch_finalize(h->partials, h->bt, h->sc, nullptr, 3, 0.0, h->stream);
+  launch_finalize(h->partials, h->bt, h->sc, nullptr, nullptr, 3, 0.0, h->stream);
   h->launches += 2;
   CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
@@ -573,26 +576,31 @@ int read_state(cmcg_handle* h) {
   return CMCG_OK;
 }
 
-// CMCG for every problem of the handle; j, e, h: one device pointer per problem.
+// CMCG for problems [0, nused) of the handle (the others are skipped by every
+// kernel); j, e, h: one device pointer per used problem.
 template <typename R>
-int solve_dev(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol, int max_iter,
-              double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im, cmcg_info* info) {
+int solve_dev(cmcg_handle* h, int nused, const double* const* j_re, const double* const* j_im, double tol,
+              int max_iter, double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im,
+              cmcg_info* info) {
   cudaEvent_t ev0, ev1;
   CK(cudaEventCreate(&ev0));
   CK(cudaEventCreate(&ev1));
   CK(cudaEventRecord(ev0, h->stream));
-  int rc = set_source<R>(h, j_re, j_im);
+  for (int p = 0; p < h->nprob; ++p) h->used_host[p] = p < nused ? 1 : 0;
+  CK(cudaMemcpyAsync(h->used, h->used_host, sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, h->stream));
+  const int32_t* mask = nused < h->nprob ? h->used : nullptr;
+  int rc = set_source<R>(h, j_re, j_im, nused);
   if (rc) return rc;
   CK(cudaMemsetAsync(h->sc, 0, sizeof(Scalars) * h->nprob, h->stream));
   // Algorithm init: G = P_psi 0, G_T = P* G, G* = G - G_T.
   CK(cudaMemsetAsync(h->Uw, 0, h->nvec * h->rsize, h->stream));
-  sweep_source<R>(h, true, false);
+  sweep_source<R>(h, true, false, mask);
   lincomb<R>(h, h->A, nullptr, nullptr, 1.0, h->Uw, 0.0, nullptr);
-  sweep_free<R>(h, true, nullptr);
+  sweep_free<R>(h, true, mask);
   lincomb<R>(h, h->Rv, h->D, h->Uw, 1.0, h->A, -1.0, h->Uw);  // R = D = G*, Uw = D
   CK(cudaMemsetAsync(h->U0, 0, h->nvec * h->rsize, h->stream));
   launch_dot<R>(h->q, (const R*)h->Rv, (const R*)h->Rv, h->wdot, h->partials, h->bt, h->stream);
-  launch_finalize(h->partials, h->bt, h->sc, h->pactive, 0, tol, h->stream);
+  launch_finalize(h->partials, h->bt, h->sc, h->pactive, h->used, 0, tol, h->stream);
   h->launches += 2;
   rc = read_state(h);
   if (rc) return rc;
@@ -609,10 +617,10 @@ int solve_dev(cmcg_handle* h, const double* const* j_re, const double* const* j_
     sweep_free<R>(h, true, h->pactive);
     launch_cg_after_adjoint<R>(h->q, (const R*)h->Uw, (const R*)h->WT, (R*)h->A, (const R*)h->D, h->wdot, h->partials,
                                h->bt, h->pactive, h->stream);
-    launch_finalize(h->partials, h->bt, h->sc, h->pactive, 1, tol, h->stream);
+    launch_finalize(h->partials, h->bt, h->sc, h->pactive, nullptr, 1, tol, h->stream);
     launch_cg_update<R>(h->q, (R*)h->U0, (R*)h->Rv, (const R*)h->D, (const R*)h->A, h->wdot, h->sc, h->partials, h->bt,
                         h->pactive, h->stream);
-    launch_finalize(h->partials, h->bt, h->sc, h->pactive, 2, tol, h->stream);
+    launch_finalize(h->partials, h->bt, h->sc, h->pactive, nullptr, 2, tol, h->stream);
     // problems that just converged keep D; the others get D = R + beta D, Uw = D
     launch_cg_direction<R>((R*)h->D, (R*)h->Uw, (const R*)h->Rv, h->sc, h->tprob, h->pactive, h->nvec, h->np,
                            h->stream);
@@ -621,12 +629,12 @@ int solve_dev(cmcg_handle* h, const double* const* j_re, const double* const* j_
     rc = read_state(h);
     if (rc) return rc;
   }
-  // Final filter F_{psi,w} U0 for every problem.
+  // Final filter F_{psi,w} U0 for every used problem.
   lincomb<R>(h, h->Uw, nullptr, nullptr, 1.0, h->U0, 0.0, nullptr);
   CK(cudaMemsetAsync(h->Fre, 0, h->nvec * h->rsize, h->stream));
   CK(cudaMemsetAsync(h->Fim, 0, h->nvec * h->rsize, h->stream));
-  sweep_source<R>(h, true, true);
-  for (int p = 0; p < h->nprob; ++p) {
+  sweep_source<R>(h, true, true, mask);
+  for (int p = 0; p < nused; ++p) {
     to_ext<R>(h, p, h->Fre, 6, 0, e_re[p], 3, 3);
     to_ext<R>(h, p, h->Fim, 6, 0, e_im[p], 3, 3);
     to_ext<R>(h, p, h->Fre, 6, 3, h_re[p], 3, 3);
@@ -640,7 +648,7 @@ int solve_dev(cmcg_handle* h, const double* const* j_re, const double* const* j_
   cudaEventDestroy(ev0);
   cudaEventDestroy(ev1);
   int worst = CMCG_OK;
-  for (int p = 0; p < h->nprob; ++p) {
+  for (int p = 0; p < nused; ++p) {
     const Scalars& S = h->sc_host[p];
     int st = S.status;
     const bool conv = S.rr0 > 0 ? std::sqrt(std::max(S.rr, 0.0)) <= tol * std::sqrt(S.rr0) : true;
@@ -667,11 +675,12 @@ void free_all(cmcg_handle* h) {
   void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
                   h->Fre, h->Fim, h->Jre, h->Jim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
                   h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
-                  h->ext0, h->ext1, h->ext2, h->ext3};
+                  h->ext0, h->ext1, h->ext2, h->ext3, h->used};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->pactive_host) cudaFreeHost(h->pactive_host);
+  if (h->used_host) cudaFreeHost(h->used_host);
   for (auto& e : h->prof_ev) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -825,11 +834,13 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
             alloc(&h->Rv, vb) && alloc(&h->D, vb) && alloc(&h->A, vb) && alloc(&h->WT, vb) &&
             alloc((void**)&h->partials, sizeof(double) * std::max<size_t>(1, bt_tet0.size())) &&
             alloc((void**)&h->sc, sizeof(Scalars) * nprob) && alloc((void**)&h->pactive, sizeof(int32_t) * nprob) &&
+            alloc((void**)&h->used, sizeof(int32_t) * nprob) &&
             alloc((void**)&h->ext0, extlen) && alloc((void**)&h->ext1, extlen) && alloc((void**)&h->ext2, extlen) &&
             alloc((void**)&h->ext3, extlen);
   if (!ok) return fail(CMCG_ERR_OUT_OF_MEMORY);
   if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars) * nprob) != cudaSuccess ||
-      cudaMallocHost((void**)&h->pactive_host, sizeof(int32_t) * nprob) != cudaSuccess)
+      cudaMallocHost((void**)&h->pactive_host, sizeof(int32_t) * nprob) != cudaSuccess ||
+      cudaMallocHost((void**)&h->used_host, sizeof(int32_t) * nprob) != cudaSuccess)
     return fail(CMCG_ERR_OUT_OF_MEMORY);
   if (cudaMemset(h->ACC, 0, vb) != cudaSuccess) return fail(CMCG_ERR_CUDA);
   rc = h->prec == CMCG_FP32 ? build_tables<float>(h) : build_tables<double>(h);
@@ -1085,28 +1096,29 @@ int cmcg_solve_batch_device(cmcg_handle* h, const double* const* j_re, const dou
   for (int p = 0; p < h->nprob; ++p)
     if (!j_re[p] || !e_re[p] || !e_im[p] || !h_re[p] || !h_im[p]) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  return DISPATCH(h, solve_dev<float>(h, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info),
-                  solve_dev<double>(h, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info));
+  return DISPATCH(h, solve_dev<float>(h, h->nprob, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info),
+                  solve_dev<double>(h, h->nprob, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info));
 }
 
-int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol, int max_iter,
-                     double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im,
-                     cmcg_info* info) {
-  if (!h || !j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0) return CMCG_ERR_INVALID_ARG;
-  for (int p = 0; p < h->nprob; ++p)
+int cmcg_solve_batch_n(cmcg_handle* h, int n, const double* const* j_re, const double* const* j_im, double tol,
+                       int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
+                       double* const* h_im, cmcg_info* info) {
+  if (!h || n < 1 || n > h->nprob || !j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0)
+    return CMCG_ERR_INVALID_ARG;
+  for (int p = 0; p < n; ++p)
     if (!j_re[p] || !e_re[p] || !e_im[p] || !h_re[p] || !h_im[p]) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
   // Staging: ext3 holds j (all re parts, then all im parts), ext0 e and ext1 h (re, then im).
   const size_t half = size_t(h->nt_total) * 3 * h->np;
-  std::vector<const double*> jr(h->nprob), ji(h->nprob);
-  std::vector<double*> er(h->nprob), ei(h->nprob), hr(h->nprob), hi(h->nprob);
-  for (int p = 0; p < h->nprob; ++p) {
-    const size_t off = size_t(h->P[p].ext0) * 3 * h->np, n = size_t(h->P[p].nt) * 3 * h->np;
-    CK(cudaMemcpyAsync(h->ext3 + off, j_re[p], n * 8, cudaMemcpyHostToDevice, h->stream));
+  std::vector<const double*> jr(n), ji(n);
+  std::vector<double*> er(n), ei(n), hr(n), hi(n);
+  for (int p = 0; p < n; ++p) {
+    const size_t off = size_t(h->P[p].ext0) * 3 * h->np, cnt = size_t(h->P[p].nt) * 3 * h->np;
+    CK(cudaMemcpyAsync(h->ext3 + off, j_re[p], cnt * 8, cudaMemcpyHostToDevice, h->stream));
     jr[p] = h->ext3 + off;
     ji[p] = nullptr;
     if (j_im && j_im[p]) {
-      CK(cudaMemcpyAsync(h->ext3 + half + off, j_im[p], n * 8, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(h->ext3 + half + off, j_im[p], cnt * 8, cudaMemcpyHostToDevice, h->stream));
       ji[p] = h->ext3 + half + off;
     }
     er[p] = h->ext0 + off;
@@ -1115,19 +1127,28 @@ int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* co
     hi[p] = h->ext1 + half + off;
   }
   int rc = DISPATCH(
-      h, solve_dev<float>(h, jr.data(), ji.data(), tol, max_iter, er.data(), ei.data(), hr.data(), hi.data(), info),
-      solve_dev<double>(h, jr.data(), ji.data(), tol, max_iter, er.data(), ei.data(), hr.data(), hi.data(), info));
+      h, solve_dev<float>(h, n, jr.data(), ji.data(), tol, max_iter, er.data(), ei.data(), hr.data(), hi.data(), info),
+      solve_dev<double>(h, n, jr.data(), ji.data(), tol, max_iter, er.data(), ei.data(), hr.data(), hi.data(), info));
   if (rc < 0) return rc;
-  for (int p = 0; p < h->nprob; ++p) {
-    const size_t n = size_t(h->P[p].nt) * 3 * h->np;
-    CK(cudaMemcpyAsync(e_re[p], er[p], n * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(e_im[p], ei[p], n * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(h_re[p], hr[p], n * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(h_im[p], hi[p], n * 8, cudaMemcpyDeviceToHost, h->stream));
+  for (int p = 0; p < n; ++p) {
+    const size_t cnt = size_t(h->P[p].nt) * 3 * h->np;
+    CK(cudaMemcpyAsync(e_re[p], er[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(e_im[p], ei[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h_re[p], hr[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h_im[p], hi[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
   }
   CK(cudaStreamSynchronize(h->stream));
   return rc;
 }
+
+int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol, int max_iter,
+                     double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im,
+                     cmcg_info* info) {
+  if (!h) return CMCG_ERR_INVALID_ARG;
+  return cmcg_solve_batch_n(h, h->nprob, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info);
+}
+
+int64_t cmcg_device_bytes(const cmcg_handle* h) { return h ? int64_t(h->bytes) : 0; }
 
 int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
                       double* e_im, double* h_re, double* h_im, cmcg_info* info) {

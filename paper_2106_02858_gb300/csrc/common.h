@@ -185,13 +185,13 @@ template <typename R>
 void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob, const int32_t* pactive,
                          int64_t n, int np, cudaStream_t s);
 // One block per problem sums its partials in a fixed order.
-//   which 0: rr = rr0 = total, active = (rr0 > 0 and tol < 1)
+//   which 0: rr = rr0 = total, active = (used (if given) and rr0 > 0 and tol < 1)
 //   which 1: dA = total, alpha = rr / dA (breakdown if dA <= 0)
 //   which 2: beta = total / rr, rr = total, iters += 1, active = (sqrt(rr) > tol sqrt(rr0))
 //   which 3: rr_new = total
 // Problems with pactive[p] == 0 are left alone for which 1 and 2.
-void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, int32_t* pactive, int which, double tol,
-                     cudaStream_t s);
+void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, int32_t* pactive, const int32_t* used,
+                     int which, double tol, cudaStream_t s);
 void upload_dot_mass(int q, const double* M);
 
 // Gauss-Legendre rule on [0, 1] (refelem.cpp).

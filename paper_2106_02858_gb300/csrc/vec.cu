@@ -191,8 +191,8 @@ __global__ void cg_direction_kernel(R* D, R* Uw, const R* Rv, const Scalars* sc,
   }
 }
 
-__global__ void finalize_kernel(const double* partials, const BlockTable bt, Scalars* sc, int32_t* pactive, int which,
-                                double tol) {
+__global__ void finalize_kernel(const double* partials, const BlockTable bt, Scalars* sc, int32_t* pactive,
+                                const int32_t* used, int which, double tol) {
   __shared__ double sh[256];
   const int p = blockIdx.x;
   const int b0 = bt.pb0[p], b1 = bt.pb0[p + 1];
@@ -216,7 +216,8 @@ __global__ void finalize_kernel(const double* partials, const BlockTable bt, Sca
     S.rr0 = tot;
     S.iters = 0;
     S.status = isfinite(tot) ? 0 : CMCG_ERR_NONFINITE;
-    if (pactive) pactive[p] = (S.status == 0 && tot > 0 && sqrt(tot) > tol * sqrt(tot)) ? 1 : 0;
+    const bool in = !used || used[p];
+    if (pactive) pactive[p] = (in && S.status == 0 && tot > 0 && sqrt(tot) > tol * sqrt(tot)) ? 1 : 0;
     return;
   }
   if (pactive && !pactive[p]) return;
@@ -305,9 +306,9 @@ void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int3
                          int64_t n, int np, cudaStream_t s) {
   cg_direction_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(D, Uw, Rv, sc, tprob, pactive, n, int64_t(6) * np * TILE);
 }
-void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, int32_t* pactive, int which, double tol,
-                     cudaStream_t s) {
-  finalize_kernel<<<bt.nprob, 256, 0, s>>>(partials, bt, sc, pactive, which, tol);
+void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, int32_t* pactive, const int32_t* used,
+                     int which, double tol, cudaStream_t s) {
+  finalize_kernel<<<bt.nprob, 256, 0, s>>>(partials, bt, sc, pactive, used, which, tol);
 }
 
 #define CMCG_INST(R)                                                                                                  \
