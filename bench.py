@@ -43,6 +43,9 @@ WORKLOAD = ("scatterer 24^3 Kuhn cube minus centred PEC cube (81,648 tets), P2 /
 CG_ITERS_FOR_REFERENCE = 35
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dg_stage_scatterer24_P2_fp32.md")
 STAGE_SRC = os.path.join(ROOT, "paper_2106_02858_gb300", "csrc", "dg_stage.cuh")
+# FP32 stage-kernel forms, indexed by cmcg_options.stage_variant - 1.
+STAGE_FORMS = ["dg_stage_kernel<float, 1>", "dg_stage_kernel<float, 3>", "dg_stage_kernel<float, 4>",
+               "dg_stage_quad<float, 4>", "dg_stage_quad<float, 5>", "dg_stage_quad<float, 6>"]
 
 
 def peaks():
@@ -153,18 +156,52 @@ def stage_algorithmic_bytes(nt: int, ndof: int, b: int) -> float:
     return field + geometry * nt
 
 
-def recorded_traffic():
-    """Per-launch DRAM bytes of the stage kernel from the committed ncu summary, if the
-    kernel source is unchanged since that capture; else None."""
+def stage_algorithmic_flops(nt: int, q: int) -> float:
+    """Algorithmic FP32 flops of one source-free nested RK4 stage (fma = 2, mul/add = 1), per
+    tetrahedron: reference derivatives of 6 components in 3 directions (18 Np^2 fma), chain rule
+    and curl with the material factor (12 flops per output value, 6 Np values), per face node the
+    6 jumps and two fluxes (64 flops, 4 Nfp nodes), the lift of 6 components (24 Np Nfp fma) and
+    the stage update (6 Np fma)."""
+    np_ = (q + 1) * (q + 2) * (q + 3) // 6
+    nfp = (q + 1) * (q + 2) // 2
+    per_tet = 36 * np_ * np_ + 72 * np_ + 256 * nfp + 48 * np_ * nfp + 12 * np_
+    return float(per_tet) * nt
+
+
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz (maximum SM clock).
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def recorded_traffic(stage_variant: int):
+    """Per-launch DRAM bytes of the stage kernel from the committed ncu summary, if that
+    summary was taken of the same kernel form with the kernel source unchanged since; else None."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     txt = open(PROFILE_SUMMARY).read()
     m_sha = re.search(r"stage kernel source sha256:\s*([0-9a-f]{64})", txt)
+    m_var = re.search(r"stage variant:\s*(\d+)", txt)
     m_tr = re.search(r"dram bytes per launch \(read \+ write\):\s*([0-9.eE+]+)", txt)
-    if not (m_sha and m_tr):
+    if not (m_sha and m_tr and m_var) or int(m_var.group(1)) != stage_variant:
         return None
     sha = hashlib.sha256(open(STAGE_SRC, "rb").read()).hexdigest()
     return float(m_tr.group(1)) if sha == m_sha.group(1) else None
+
+
+# ---------------------------------------------------------------------------------------------
+# Replicas (N > 1): every rank solves its own problem; no data-path collective.
+# ---------------------------------------------------------------------------------------------
+
+def replica_throughput(local_s: float, steps: int, world: int, device=None):
+    """Whole-job time = the slowest rank's time (MAX all-reduce of one scalar after
+    the timed region), and throughput = solves of all ranks / that time."""
+    total_s = float(local_s)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return total_s, steps * world / total_s
 
 
 # ---------------------------------------------------------------------------------------------
@@ -205,7 +242,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     prob = I.scatterer_sphere(seed=args.seed + rank)
-    h32, _m32 = cmcg.create_for_problem(prob, precision=cmcg.CMCG_FP32, device=local_rank)
+    h32, _m32 = cmcg.create_for_problem(prob, precision=cmcg.CMCG_FP32, device=local_rank,
+                                        stage_variant=args.stage_variant)
     stream = torch.cuda.current_stream(dev)
     cmcg.cmcg_set_stream(h32, stream)
     jr = torch.from_numpy(prob.j_re).to(dev)
@@ -242,12 +280,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     cmcg.cmcg_profile_enable(h32, False)
     clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    total_s = sum(step_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([total_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    value = args.steps * world / total_s
+    total_s, value = replica_throughput(sum(step_ms) / 1e3, args.steps, world, dev)
     iters = infos[-1].iters
     periods = 3 + 2 * iters
     dof_updates = prob.ndof * h32.steps * periods
@@ -263,12 +296,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         t0 = time.perf_counter()
         cmcg.cmcg_solve(h32, jr_h, ji_h, CG_TOL, MAX_ITER)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    if world > 1:
-        t = torch.tensor([sum(e2e_ms) / 1e3], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    else:
-        e2e_total = sum(e2e_ms) / 1e3
+    e2e_total, e2e_value = replica_throughput(sum(e2e_ms) / 1e3, len(e2e_ms), world, dev)
     nj = prob.nt * 3 * prob.np_ * 8
     h2d, d2h = 2 * nj, 4 * nj
 
@@ -299,8 +327,14 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     stage_us = free_ms * 1e3 / max(free_stages, 1)
     alg = stage_algorithmic_bytes(prob.nt, prob.ndof, 4)
     achieved = alg / (stage_us * 1e-6) / 1e9
+    form, form_us = cmcg.cmcg_get_tuning(h32)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(), "kernel": "dg_stage_kernel<float> (P2, nested RK4 stage)",
+                "traffic": recorded_traffic(form + 1), "kernel": f"{STAGE_FORMS[form]} (P2, nested RK4 stage)",
+                "stage_variant": form + 1, "tuning_us": form_us,
+                "alu": {"achieved": stage_algorithmic_flops(prob.nt, prob.order) / (stage_us * 1e-6) / 1e12,
+                        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "frac": stage_algorithmic_flops(prob.nt, prob.order) / (stage_us * 1e-6) / 1e12
+                        / FP32_PEAK_TFLOPS, "peak_source": "unit counts x maximum SM clock"},
                 "algorithmic_bytes_per_launch": alg, "avg_launch_us": stage_us, "peak_source": peak_kind}
 
     cpu = None
@@ -329,7 +363,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "rel_l2_vs_fp64": fp64["rel_l2"] if fp64 else None,
             "fp64_plain_solves_per_s": 1e3 / fp64["ms"] if fp64 else None,
             "fp64_plain_iters": fp64["iters"] if fp64 else None,
-            "e2e": {"value": args.steps * world / e2e_total, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "roofline": roofline,

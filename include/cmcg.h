@@ -42,7 +42,12 @@
  * negative CMCG_ERR_* code on failure (output buffers are then unspecified
  * for device entry points and untouched for host entry points), or
  * CMCG_NOT_CONVERGED (> 0) when cmcg_solve reached max_iter; its outputs are
- * then valid (Algorithm cmcg returns the last iterate).
+ * then valid (Algorithm cmcg returns the last iterate).  The solves stop a
+ * problem with CMCG_ERR_UNSTABLE when a CG direction D has
+ * |(I - P) D| > 100 |D| in the (eps, mu) norm (the period map grows the
+ * energy by orders of magnitude: a step beyond the stability limit, e.g. a
+ * forced steps_per_period), CMCG_ERR_CG_BREAKDOWN when (D, A) <= 0 and
+ * CMCG_ERR_NONFINITE when a reduction is not finite.
  *
  * Threading: one handle per host thread at a time.
  */
@@ -103,12 +108,19 @@ typedef struct cmcg_mesh {
  *                     device memory than this.
  *   device:           CUDA device ordinal.
  *   stage_variant:    0 = time the stage-kernel forms on this mesh at
- *                     creation and keep the fastest; k > 0 forces form k - 1:
- *                     0..2 = scalar kernel (two threads per tetrahedron) with
- *                     at least 1, 3, 4 resident 128-thread blocks per SM
- *                     (FP64: 0 only); 3 (FP32) = packed kernel, two
- *                     tetrahedra per lane with f32x2 FMAs.  Results do not
- *                     depend on it beyond rounding. */
+ *                     creation and keep the fastest; k > 0 forces form k - 1.
+ *                     FP32: 0, 1, 2 = two threads per tetrahedron (E / H)
+ *                     with at least 1, 3, 4 resident 128-thread blocks per
+ *                     SM; 3, 4, 5 = four threads per tetrahedron (E / H x
+ *                     node half) with at least 4, 5, 6.  FP64: 0 = two
+ *                     threads per tetrahedron; 1, 2 = four threads with at
+ *                     least 2, 3.  Other k: CMCG_ERR_INVALID_ARG.  Results do
+ *                     not depend on it beyond rounding.
+ *   stage_overlap:    0 = decide by timing when the form is timed (on when
+ *                     the form is forced); 1 = on; 2 = off.  On: each stage
+ *                     is launched with programmatic stream serialisation, so
+ *                     its blocks start and load the mesh data while the
+ *                     previous stage finishes.  Results are identical. */
 typedef struct cmcg_options {
   int order;
   int precision;
@@ -118,7 +130,8 @@ typedef struct cmcg_options {
   int64_t hbm_budget_bytes;
   int device;
   int stage_variant;
-  int reserved[6];
+  int stage_overlap;
+  int reserved[5];
 } cmcg_options;
 
 /* Per-solve report. */
@@ -194,8 +207,9 @@ int cmcg_set_stream(cmcg_handle* h, void* stream);
 
 /* Stage-kernel form in use (0-based, as stage_variant - 1) and, when it was
  * chosen by timing at creation, the measured microseconds per stage of each
- * form (8 entries: [0..2] scalar variants, [3] packed kernel; -1 where not
- * timed).  Any pointer may be NULL. */
+ * form (8 entries: [0..5] indexed by form, see stage_variant; [6] the chosen
+ * form with stage_overlap on; -1 where not timed or rejected by the device).
+ * Any pointer may be NULL. */
 int cmcg_get_tuning(const cmcg_handle* h, int* variant, double* us_per_stage);
 
 /* Sizes of the handle: nt, Np, M (steps per period), dt, number of doubles of

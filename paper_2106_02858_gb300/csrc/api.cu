@@ -86,8 +86,8 @@ struct cmcg_handle {
   double *ext0 = nullptr, *ext1 = nullptr, *ext2 = nullptr, *ext3 = nullptr;
   int64_t launches = 0;
   size_t bytes = 0;
-  int variant = 0;      // occupancy variant of the scalar stage kernel
-  int packed_minb = 0;  // > 0 (FP32): stages run on the packed two-tetrahedra-per-lane kernel
+  int form = 0;      // stage-kernel form (see launch_stage)
+  bool pdl = false;  // stages launched with programmatic stream serialisation
   double tune_us[8];
   // sweep profiling
   bool prof = false;
@@ -259,18 +259,9 @@ void stage(cmcg_handle* h, StageArgs<R>& a) {
   a.nbr = h->nbr;
   a.nti = h->nti;
   a.tprob = h->tprob;
-  if constexpr (sizeof(R) == 4) {
-    if (h->packed_minb > 0) {
-      if (h->q == 1) launch_stage_packed<1>(a, h->stream, h->packed_minb);
-      else if (h->q == 2) launch_stage_packed<2>(a, h->stream, h->packed_minb);
-      else launch_stage_packed<3>(a, h->stream, h->packed_minb);
-      h->launches++;
-      return;
-    }
-  }
-  if (h->q == 1) launch_stage<1, R>(a, h->stream, h->variant);
-  else if (h->q == 2) launch_stage<2, R>(a, h->stream, h->variant);
-  else launch_stage<3, R>(a, h->stream, h->variant);
+  if (h->q == 1) launch_stage<1, R>(a, h->stream, h->form, h->pdl);
+  else if (h->q == 2) launch_stage<2, R>(a, h->stream, h->form, h->pdl);
+  else launch_stage<3, R>(a, h->stream, h->form, h->pdl);
   h->launches++;
 }
 
@@ -381,11 +372,10 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
 }
 
 // Times the stage-kernel forms on this batch with a nested source-free stage
-// on zero fields (3 warm-up + 12 timed launches each): the scalar kernel at
-// each occupancy variant and, in FP32, the packed kernel; keeps the fastest.
-// tune_us[0..2]: scalar variants, tune_us[3]: packed.
+// on zero fields (3 warm-up + 12 timed launches each) and keeps the fastest;
+// tune_us[f] is the time of form f (-1: not timed or rejected by the device).
 template <typename R>
-int autotune(cmcg_handle* h, int nvariants) {
+int autotune(cmcg_handle* h, int nforms, int overlap) {
   for (double& x : h->tune_us) x = -1;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -421,27 +411,29 @@ int autotune(cmcg_handle* h, int nvariants) {
     return CMCG_OK;
   };
   double best = 1e300;
-  int bestv = 0;
-  h->packed_minb = 0;
-  for (int v = 0; v < nvariants; ++v) {
-    h->variant = v;
+  int bestf = 0;
+  h->pdl = false;
+  for (int f = 0; f < nforms; ++f) {
+    h->form = f;
     double us;
     int rc = time_one(&us);
     if (rc) return rc;
-    h->tune_us[v] = us;
+    h->tune_us[f] = us;
     if (us >= 0 && us < best) {
       best = us;
-      bestv = v;
+      bestf = f;
     }
   }
-  h->variant = bestv;
-  if (sizeof(R) == 4) {
-    h->packed_minb = 2;
+  h->form = bestf;
+  if (overlap == 0) {  // the chosen form with overlapped stage launches
+    h->pdl = true;
     double us;
     int rc = time_one(&us);
     if (rc) return rc;
-    h->tune_us[3] = us;
-    if (!(us >= 0 && us < best)) h->packed_minb = 0;
+    h->tune_us[6] = us;
+    h->pdl = us >= 0 && us < best;
+  } else {
+    h->pdl = overlap == 1;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -832,7 +824,7 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
   bool ok = alloc(&h->Uw, vb) && alloc(&h->vA, vb) && alloc(&h->vB, vb) && alloc(&h->ACC, vb) && alloc(&h->Fre, vb) &&
             alloc(&h->Fim, vb) && alloc(&h->Jre, jb) && alloc(&h->Jim, jb) && alloc(&h->U0, vb) &&
             alloc(&h->Rv, vb) && alloc(&h->D, vb) && alloc(&h->A, vb) && alloc(&h->WT, vb) &&
-            alloc((void**)&h->partials, sizeof(double) * std::max<size_t>(1, bt_tet0.size())) &&
+            alloc((void**)&h->partials, sizeof(double) * 2 * std::max<size_t>(1, bt_tet0.size())) &&
             alloc((void**)&h->sc, sizeof(Scalars) * nprob) && alloc((void**)&h->pactive, sizeof(int32_t) * nprob) &&
             alloc((void**)&h->used, sizeof(int32_t) * nprob) &&
             alloc((void**)&h->ext0, extlen) && alloc((void**)&h->ext1, extlen) && alloc((void**)&h->ext2, extlen) &&
@@ -846,13 +838,13 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
   rc = h->prec == CMCG_FP32 ? build_tables<float>(h) : build_tables<double>(h);
   if (rc) return fail(rc);
   if (opt.stage_variant > 0) {
-    const int nv = h->prec == CMCG_FP32 ? STAGE_VARIANTS_F32 : 1;
-    const int k = opt.stage_variant - 1;
-    if (k < nv) h->variant = k;
-    else if (k == 3 && h->prec == CMCG_FP32) h->packed_minb = 2;
-    else return fail(CMCG_ERR_INVALID_ARG);
+    const int nf = h->prec == CMCG_FP32 ? STAGE_FORMS_F32 : STAGE_FORMS_F64;
+    if (opt.stage_variant > nf) return fail(CMCG_ERR_INVALID_ARG);
+    h->form = opt.stage_variant - 1;
+    h->pdl = opt.stage_overlap != 2;
   } else {
-    rc = h->prec == CMCG_FP32 ? autotune<float>(h, STAGE_VARIANTS_F32) : autotune<double>(h, 1);
+    rc = h->prec == CMCG_FP32 ? autotune<float>(h, STAGE_FORMS_F32, opt.stage_overlap)
+                              : autotune<double>(h, STAGE_FORMS_F64, opt.stage_overlap);
     if (rc) return fail(rc);
   }
   h->launches = 0;
@@ -975,7 +967,7 @@ int64_t cmcg_kernel_launches(const cmcg_handle* h) { return h ? h->launches : 0;
 
 int cmcg_get_tuning(const cmcg_handle* h, int* variant, double* us_per_stage) {
   if (!h) return CMCG_ERR_INVALID_ARG;
-  if (variant) *variant = h->packed_minb > 0 ? 3 : h->variant;
+  if (variant) *variant = h->form;
   if (us_per_stage)
     for (int i = 0; i < 8; ++i) us_per_stage[i] = h->tune_us[i];
   return CMCG_OK;

@@ -125,16 +125,18 @@ struct StageArgs {
 };
 
 // Kernel launchers, one translation unit per order.
-// variant: occupancy variant of the stage kernel (FP32: 0..2 = at least 1, 3, 4
-// resident 128-thread blocks per SM; FP64 has one variant).
-constexpr int STAGE_VARIANTS_F32 = 3;
+// form: stage-kernel form.  FP32: 0, 1, 2 = two threads per tetrahedron with at
+// least 1, 3, 4 resident 128-thread blocks per SM; 3, 4, 5 = four threads per
+// tetrahedron with at least 4, 5, 6.  FP64: 0 = two threads per tetrahedron,
+// 1, 2 = four threads per tetrahedron with at least 2, 3 blocks.  pdl: launch
+// with programmatic stream serialisation (the stage overlaps the previous
+// stage's tail).
+constexpr int STAGE_FORMS_F32 = 6;
+constexpr int STAGE_FORMS_F64 = 3;
 template <int Q, typename R>
-void launch_stage(const StageArgs<R>& a, cudaStream_t s, int variant);
+void launch_stage(const StageArgs<R>& a, cudaStream_t s, int form, bool pdl);
 template <int Q>
 void upload_constants(const RefMats& rm);
-// Packed FP32 stage kernel (two tetrahedra per lane, f32x2 FMA, at least 2 resident blocks).
-template <int Q>
-void launch_stage_packed(const StageArgs<float>& a, cudaStream_t s, int minb);
 
 // Vector kernels (vec.cu).
 struct Scalars {

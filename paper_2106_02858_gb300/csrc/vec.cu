@@ -81,6 +81,7 @@ __device__ __forceinline__ double block_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();  // a previous call's reads of sh are done
   if (l == 0) sh[w] = v;
   __syncthreads();
   double s = 0;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(DOT_THREADS) cg_after_adjoint_kernel(const R* 
   constexpr int NP = np_of(Q);
   const bool act = !pactive || pactive[bt.prob[blockIdx.x]];
   const int64_t t = block_tet(bt);
-  double acc = 0;
+  double acc = 0, dd = 0;
   if (act && t >= 0) {
     const int64_t tile = t >> 5;
     const int lane = int(t & 31);
@@ -137,9 +138,14 @@ __global__ void __launch_bounds__(DOT_THREADS) cg_after_adjoint_kernel(const R* 
 #pragma unroll
     for (int k = 0; k < 6 * NP; ++k) A[base + k * TILE] = R(double(Uw[base + k * TILE]) - double(WT[base + k * TILE]));
     acc = tet_dot<Q, R>(D, A, tile, lane, wdot);
+    dd = tet_dot<Q, R>(D, D, tile, lane, wdot);
   }
   const double s = block_sum(acc);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  const double s2 = block_sum(dd);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = s;
+    partials[gridDim.x + blockIdx.x] = s2;
+  }
 }
 
 // U0 += alpha_p D; R -= alpha_p A; partial (R, R).
@@ -196,16 +202,23 @@ __global__ void finalize_kernel(const double* partials, const BlockTable bt, Sca
   __shared__ double sh[256];
   const int p = blockIdx.x;
   const int b0 = bt.pb0[p], b1 = bt.pb0[p + 1];
-  double s = 0;
-  for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += partials[i];
-  sh[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+  auto reduce = [&](const double* part) {
+    double s = 0;
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += part[i];
+    sh[threadIdx.x] = s;
     __syncthreads();
-  }
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    const double r = sh[0];
+    __syncthreads();
+    return r;
+  };
+  const double tot = reduce(partials);
+  // which == 1: (D, D)_M of the same blocks, stored after the (D, A) partials
+  const double dd = which == 1 ? reduce(partials + bt.nblk) : 0.0;
   if (threadIdx.x != 0) return;
-  const double tot = sh[0];
   Scalars& S = sc[p];
   if (which == 3) {
     S.rr_new = tot;
@@ -228,7 +241,15 @@ __global__ void finalize_kernel(const double* partials, const BlockTable bt, Sca
   }
   if (which == 1) {
     S.dA = tot;
-    if (!(tot > 0)) {
+    // (D, A) = |(I - P) D|^2 <= (1 + |P|)^2 |D|^2.  A CFL-stable period map is not a
+    // contraction in this norm (non-normal transient growth; |P D| / |D| reaches about 3
+    // along the CG directions of the test meshes), but a step beyond the stability limit
+    // grows by orders of magnitude per period: |(I - P) D| > 100 |D| means |P| > 99.
+    if (tot > 1e4 * dd) {
+      S.status = CMCG_ERR_UNSTABLE;
+      S.alpha = 0;
+      if (pactive) pactive[p] = 0;
+    } else if (!(tot > 0)) {
       S.status = CMCG_ERR_CG_BREAKDOWN;
       S.alpha = 0;
       if (pactive) pactive[p] = 0;

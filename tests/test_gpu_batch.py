@@ -58,12 +58,14 @@ def _uneven(q, seed=0):
     return out
 
 
+@pytest.mark.parametrize("threads", [2, 4])
 @pytest.mark.parametrize("q", [1, 2, 3])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_uneven_batch_alone_vs_in_the_mix(lib, q, prec):
+def test_uneven_batch_alone_vs_in_the_mix(lib, q, prec, threads):
     probs = _uneven(q)
     P = lib.CMCG_FP64 if prec == "fp64" else lib.CMCG_FP32
-    form = 2 if prec == "fp32" else 1  # the same kernel form alone and in the mix
+    # the same kernel form alone and in the mix: two or four threads per tetrahedron
+    form = {("fp32", 2): 2, ("fp32", 4): 5, ("fp64", 2): 1, ("fp64", 4): 2}[prec, threads]
     h, _m = _create_batch(lib, probs, P, stage_variant=form)
     assert lib.cmcg_batch_size(h) == len(probs)
     steps = [lib.cmcg_get_problem(h, p)[1] for p in range(len(probs))]

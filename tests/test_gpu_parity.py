@@ -214,8 +214,8 @@ def test_hbm_budget_is_enforced(lib):
 @pytest.mark.parametrize("q", [1, 2, 3])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_every_stage_kernel_form_matches_oracle(lib, q, prec):
-    """Each forced stage-kernel form (scalar occupancy variants, packed FP32 kernel) gives the
-    oracle's sweeps: the autotuner's choice cannot change results."""
+    """Each forced stage-kernel form (two or four threads per tetrahedron, each at several
+    occupancies) gives the oracle's sweeps: the autotuner's choice cannot change results."""
     from oracle.timestep import Stepper
     p = _problem("scatterer8", q) if q < 3 else _problem("cube3", q)
     g = _geo(p)
@@ -224,7 +224,7 @@ def test_every_stage_kernel_form_matches_oracle(lib, q, prec):
     U = I.random_field(rng, p.nt, q)
     refF, refA = st.P(U), st.P_star(U)
     tol = 1e-12 if prec == "fp64" else 1e-5
-    forms = [1, 2, 3, 4, 5] if prec == "fp32" else [1, 2, 4]
+    forms = [1, 2, 3, 4, 5, 6, 7] if prec == "fp32" else [1, 2, 3, 4]
     tried = 0
     for k in forms:
         try:
@@ -237,4 +237,30 @@ def test_every_stage_kernel_form_matches_oracle(lib, q, prec):
         assert _rel(lib.dgtd_period_forward(h, U), refF, g) < tol, k
         assert _rel(lib.dgtd_period_adjoint(h, U), refA, g) < tol, k
         h.close()
-    assert tried == (4 if prec == "fp32" else 1)
+    assert tried == (6 if prec == "fp32" else 3)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_unstable_time_step_is_reported(lib, prec):
+    """A step far beyond the CFL limit (M = 3 instead of 16) makes the period map grow the
+    (eps, mu)-norm by orders of magnitude (the oracle's P multiplies that of a random field by
+    more than 100); the solve stops in its first CG iteration with CMCG_ERR_UNSTABLE instead of
+    iterating on garbage, while the CFL step, whose period map is not a contraction either
+    (transient growth up to about 3), raises no false alarm."""
+    from oracle.timestep import Stepper
+    p = _problem("cube3", 1)
+    g = _geo(p)
+    st = Stepper(g, p.omega, M=3)
+    U = I.random_field(np.random.default_rng(5), p.nt, 1)
+    from oracle.dg import norm
+    assert norm(st.P(U), g) > 100 * norm(U, g)
+    P = lib.CMCG_FP64 if prec == "fp64" else lib.CMCG_FP32
+    h, _ = lib.create_for_problem(p, precision=P, steps_per_period=3)
+    with pytest.raises(lib.CMCGError) as ei:
+        lib.cmcg_solve(h, p.j_re, p.j_im, 1e-8, 50)
+    assert ei.value.code == lib.CMCG_ERR_UNSTABLE
+    h.close()
+    h, _ = lib.create_for_problem(p, precision=P)  # the CFL step: no false alarm
+    e, hh, info = lib.cmcg_solve(h, p.j_re, p.j_im, 1e-6, 400)
+    assert info.status == lib.CMCG_OK
+    h.close()

@@ -75,6 +75,9 @@ def test_validate_rejects_broken_meshes(lib):
     assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, -1.0, opt)[0] == lib.CMCG_ERR_INVALID_ARG
     assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, 1.0,
                              lib.cmcg_default_options(order=4))[0] == lib.CMCG_ERR_INVALID_ARG
+    for bad_opt in (dict(stage_variant=-1), dict(stage_overlap=3), dict(stage_overlap=-1)):
+        assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, 1.0,
+                                 lib.cmcg_default_options(order=1, **bad_opt))[0] == lib.CMCG_ERR_INVALID_ARG
     tags = m.tags.copy()
     tags[0, 0] = 7
     assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, tags), eps, mu, 1.0, opt)[0] == lib.CMCG_ERR_INVALID_ARG
