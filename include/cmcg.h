@@ -311,6 +311,19 @@ int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, do
  * counter kept on the host at every launch). */
 int64_t cmcg_kernel_launches(const cmcg_handle* h);
 
+/* Limiting-amplitude baseline ("full wave", FW, Section 6): marches the
+ * scheme with the time-harmonic source from rest for `periods` periods,
+ * U = P_{psi,w}^periods 0, then returns the filtered field F_{psi,w} U of one
+ * further period (Section 2.1).  Cost: periods + 1 source sweeps; no CG.  By
+ * the limiting amplitude principle (Section 1) the result tends to the CMCG
+ * result as periods grows when transients decay.  periods >= 0; buffers as in
+ * cmcg_solve.  cmcg_fw_solve_batch runs every problem of a batch handle
+ * (arrays of nprob host pointers, as in cmcg_solve_batch). */
+int cmcg_fw_solve(cmcg_handle* h, const double* j_re, const double* j_im, int periods, double* e_re, double* e_im,
+                  double* h_re, double* h_im);
+int cmcg_fw_solve_batch(cmcg_handle* h, int periods, const double* const* j_re, const double* const* j_im,
+                        double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im);
+
 /* Sweep timing.  cmcg_profile_enable(h, 1) resets the counters and makes
  * every later period sweep record a CUDA event on the handle's stream before
  * its first and after its last stage; 0 stops recording.  cmcg_profile_read

@@ -98,6 +98,9 @@ def _load() -> C.CDLL:
                                          C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp),
                                          C.POINTER(cmcg_info)]),
         "cmcg_device_bytes": (C.c_int64, [_vp]),
+        "cmcg_fw_solve": (C.c_int, [_vp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]),
+        "cmcg_fw_solve_batch": (C.c_int, [_vp, C.c_int, C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp),
+                                          C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp)]),
         "cmcg_server_default_options": (None, [C.POINTER(cmcg_server_options)]),
         "cmcg_server_create": (C.c_int, [C.POINTER(cmcg_server_options), C.POINTER(_vp)]),
         "cmcg_server_add_model": (C.c_int, [_vp, C.POINTER(cmcg_mesh), _dp, _dp, C.c_double, C.c_int, C.c_int,
@@ -141,7 +144,7 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_solve_device", "cmcg_kernel_launches", "cmcg_profile_enable", "cmcg_profile_read",
             "cmcg_inner", "cmcg_inner_noalloc", "cmcg_get_tuning", "cmcg_create_batch", "cmcg_batch_size",
             "cmcg_get_problem", "cmcg_solve_batch", "cmcg_solve_batch_device", "cmcg_solve_batch_n",
-            "cmcg_device_bytes", "cmcg_server_default_options", "cmcg_server_create", "cmcg_server_add_model",
+            "cmcg_device_bytes", "cmcg_fw_solve", "cmcg_fw_solve_batch", "cmcg_server_default_options", "cmcg_server_create", "cmcg_server_add_model",
             "cmcg_server_submit", "cmcg_server_poll", "cmcg_server_stats", "cmcg_server_destroy")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
@@ -447,6 +450,29 @@ def cmcg_solve(h: Handle, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 10
     _check(_lib.cmcg_solve(h.ptr, _ptr(jr), _ptr(ji), float(tol), int(max_iter), _ptr(er), _ptr(ei), _ptr(hr),
                            _ptr(hi), C.byref(info)), "cmcg_solve", allow_not_converged=True)
     return er + 1j * ei, hr + 1j * hi, info
+
+
+def cmcg_fw_solve(h: Handle, j_re, j_im=None, periods: int = 1):
+    """Limiting-amplitude baseline: F_psi(P_psi^periods 0).  Returns (e, h_field) complex (nt, 3, Np)."""
+    jr, ji = _field(h, j_re, 3, "j_re"), _field(h, j_im, 3, "j_im")
+    er, ei, hr, hi = (np.empty((h.nt, 3, h.np)) for _ in range(4))
+    _check(_lib.cmcg_fw_solve(h.ptr, _ptr(jr), _ptr(ji), int(periods), _ptr(er), _ptr(ei), _ptr(hr), _ptr(hi)),
+           "cmcg_fw_solve")
+    return er + 1j * ei, hr + 1j * hi
+
+
+def cmcg_fw_solve_batch(h: Handle, j_re, j_im=None, periods: int = 1):
+    """Every problem of a batch handle; lists in and out as in cmcg_solve_batch."""
+    n = len(h.problems)
+    jr = [_f64(j_re[p], (h.problems[p][0], 3, h.np), "j_re") for p in range(n)]
+    ji = [None if (j_im is None or j_im[p] is None) else _f64(j_im[p], (h.problems[p][0], 3, h.np), "j_im")
+          for p in range(n)]
+    outs = [[np.empty((h.problems[p][0], 3, h.np)) for p in range(n)] for _ in range(4)]
+    P = C.POINTER(C.c_double)
+    arr = lambda xs: (P * n)(*[_ptr(x) if x is not None else P() for x in xs])
+    _check(_lib.cmcg_fw_solve_batch(h.ptr, int(periods), arr(jr), arr(ji), arr(outs[0]), arr(outs[1]), arr(outs[2]),
+                                    arr(outs[3])), "cmcg_fw_solve_batch")
+    return [outs[0][p] + 1j * outs[1][p] for p in range(n)], [outs[2][p] + 1j * outs[3][p] for p in range(n)]
 
 
 def cmcg_solve_device(h: Handle, j_re, j_im, tol: float, max_iter: int, e_re, e_im, h_re, h_im) -> cmcg_info:

@@ -663,6 +663,28 @@ int solve_dev(cmcg_handle* h, int nused, const double* const* j_re, const double
   return worst;
 }
 
+// Limiting amplitude ("full wave", Section 6): U = P_psi^periods 0, then
+// F_psi U, for every problem of the handle.
+template <typename R>
+int fw_dev(cmcg_handle* h, int periods, const double* const* j_re, const double* const* j_im, double* const* e_re,
+           double* const* e_im, double* const* h_re, double* const* h_im) {
+  int rc = set_source<R>(h, j_re, j_im, h->nprob);
+  if (rc) return rc;
+  CK(cudaMemsetAsync(h->Uw, 0, h->nvec * h->rsize, h->stream));
+  for (int l = 0; l < periods; ++l) sweep_source<R>(h, true, false, nullptr);
+  CK(cudaMemsetAsync(h->Fre, 0, h->nvec * h->rsize, h->stream));
+  CK(cudaMemsetAsync(h->Fim, 0, h->nvec * h->rsize, h->stream));
+  sweep_source<R>(h, true, true, nullptr);
+  for (int p = 0; p < h->nprob; ++p) {
+    to_ext<R>(h, p, h->Fre, 6, 0, e_re[p], 3, 3);
+    to_ext<R>(h, p, h->Fim, 6, 0, e_im[p], 3, 3);
+    to_ext<R>(h, p, h->Fre, 6, 3, h_re[p], 3, 3);
+    to_ext<R>(h, p, h->Fim, 6, 3, h_im[p], 3, 3);
+  }
+  CK(cudaGetLastError());
+  return CMCG_OK;
+}
+
 void free_all(cmcg_handle* h) {
   void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
                   h->Fre, h->Fim, h->Jre, h->Jim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
@@ -1092,45 +1114,104 @@ int cmcg_solve_batch_device(cmcg_handle* h, const double* const* j_re, const dou
                   solve_dev<double>(h, h->nprob, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info));
 }
 
-int cmcg_solve_batch_n(cmcg_handle* h, int n, const double* const* j_re, const double* const* j_im, double tol,
-                       int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
-                       double* const* h_im, cmcg_info* info) {
-  if (!h || n < 1 || n > h->nprob || !j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0)
-    return CMCG_ERR_INVALID_ARG;
-  for (int p = 0; p < n; ++p)
-    if (!j_re[p] || !e_re[p] || !e_im[p] || !h_re[p] || !h_im[p]) return CMCG_ERR_INVALID_ARG;
-  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  // Staging: ext3 holds j (all re parts, then all im parts), ext0 e and ext1 h (re, then im).
+}  // extern "C"
+
+namespace {
+
+// Host-buffer entry points: sources copied into the staging vectors (ext3: all
+// real parts, then all imaginary parts), results staged in ext0 (e) and ext1 (h).
+struct HostIO {
+  std::vector<const double*> jr, ji;
+  std::vector<double*> er, ei, hr, hi;
+};
+
+int stage_host_inputs(cmcg_handle* h, int n, const double* const* j_re, const double* const* j_im, HostIO& io) {
   const size_t half = size_t(h->nt_total) * 3 * h->np;
-  std::vector<const double*> jr(n), ji(n);
-  std::vector<double*> er(n), ei(n), hr(n), hi(n);
+  io.jr.assign(n, nullptr);
+  io.ji.assign(n, nullptr);
+  io.er.assign(n, nullptr);
+  io.ei.assign(n, nullptr);
+  io.hr.assign(n, nullptr);
+  io.hi.assign(n, nullptr);
   for (int p = 0; p < n; ++p) {
     const size_t off = size_t(h->P[p].ext0) * 3 * h->np, cnt = size_t(h->P[p].nt) * 3 * h->np;
     CK(cudaMemcpyAsync(h->ext3 + off, j_re[p], cnt * 8, cudaMemcpyHostToDevice, h->stream));
-    jr[p] = h->ext3 + off;
-    ji[p] = nullptr;
+    io.jr[p] = h->ext3 + off;
     if (j_im && j_im[p]) {
       CK(cudaMemcpyAsync(h->ext3 + half + off, j_im[p], cnt * 8, cudaMemcpyHostToDevice, h->stream));
-      ji[p] = h->ext3 + half + off;
+      io.ji[p] = h->ext3 + half + off;
     }
-    er[p] = h->ext0 + off;
-    ei[p] = h->ext0 + half + off;
-    hr[p] = h->ext1 + off;
-    hi[p] = h->ext1 + half + off;
+    io.er[p] = h->ext0 + off;
+    io.ei[p] = h->ext0 + half + off;
+    io.hr[p] = h->ext1 + off;
+    io.hi[p] = h->ext1 + half + off;
   }
-  int rc = DISPATCH(
-      h, solve_dev<float>(h, n, jr.data(), ji.data(), tol, max_iter, er.data(), ei.data(), hr.data(), hi.data(), info),
-      solve_dev<double>(h, n, jr.data(), ji.data(), tol, max_iter, er.data(), ei.data(), hr.data(), hi.data(), info));
-  if (rc < 0) return rc;
+  return CMCG_OK;
+}
+
+int copy_host_outputs(cmcg_handle* h, int n, const HostIO& io, double* const* e_re, double* const* e_im,
+                      double* const* h_re, double* const* h_im) {
   for (int p = 0; p < n; ++p) {
     const size_t cnt = size_t(h->P[p].nt) * 3 * h->np;
-    CK(cudaMemcpyAsync(e_re[p], er[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(e_im[p], ei[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(h_re[p], hr[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(h_im[p], hi[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(e_re[p], io.er[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(e_im[p], io.ei[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h_re[p], io.hr[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h_im[p], io.hi[p], cnt * 8, cudaMemcpyDeviceToHost, h->stream));
   }
   CK(cudaStreamSynchronize(h->stream));
-  return rc;
+  return CMCG_OK;
+}
+
+bool host_args_ok(const cmcg_handle* h, int n, const double* const* j_re, double* const* e_re, double* const* e_im,
+                  double* const* h_re, double* const* h_im) {
+  if (!h || n < 1 || n > h->nprob || !j_re || !e_re || !e_im || !h_re || !h_im) return false;
+  for (int p = 0; p < n; ++p)
+    if (!j_re[p] || !e_re[p] || !e_im[p] || !h_re[p] || !h_im[p]) return false;
+  return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cmcg_solve_batch_n(cmcg_handle* h, int n, const double* const* j_re, const double* const* j_im, double tol,
+                       int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
+                       double* const* h_im, cmcg_info* info) {
+  if (!host_args_ok(h, n, j_re, e_re, e_im, h_re, h_im) || !(tol >= 0) || max_iter < 0) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  HostIO io;
+  int rc = stage_host_inputs(h, n, j_re, j_im, io);
+  if (rc) return rc;
+  rc = DISPATCH(h,
+                solve_dev<float>(h, n, io.jr.data(), io.ji.data(), tol, max_iter, io.er.data(), io.ei.data(),
+                                 io.hr.data(), io.hi.data(), info),
+                solve_dev<double>(h, n, io.jr.data(), io.ji.data(), tol, max_iter, io.er.data(), io.ei.data(),
+                                  io.hr.data(), io.hi.data(), info));
+  if (rc < 0) return rc;
+  const int rc2 = copy_host_outputs(h, n, io, e_re, e_im, h_re, h_im);
+  return rc2 ? rc2 : rc;
+}
+
+int cmcg_fw_solve_batch(cmcg_handle* h, int periods, const double* const* j_re, const double* const* j_im,
+                        double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im) {
+  if (!host_args_ok(h, h ? h->nprob : 0, j_re, e_re, e_im, h_re, h_im) || periods < 0) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  HostIO io;
+  int rc = stage_host_inputs(h, h->nprob, j_re, j_im, io);
+  if (rc) return rc;
+  rc = DISPATCH(h,
+                fw_dev<float>(h, periods, io.jr.data(), io.ji.data(), io.er.data(), io.ei.data(), io.hr.data(),
+                              io.hi.data()),
+                fw_dev<double>(h, periods, io.jr.data(), io.ji.data(), io.er.data(), io.ei.data(), io.hr.data(),
+                               io.hi.data()));
+  if (rc < 0) return rc;
+  return copy_host_outputs(h, h->nprob, io, e_re, e_im, h_re, h_im);
+}
+
+int cmcg_fw_solve(cmcg_handle* h, const double* j_re, const double* j_im, int periods, double* e_re, double* e_im,
+                  double* h_re, double* h_im) {
+  if (!single(h)) return CMCG_ERR_INVALID_ARG;
+  return cmcg_fw_solve_batch(h, periods, &j_re, &j_im, &e_re, &e_im, &h_re, &h_im);
 }
 
 int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol, int max_iter,

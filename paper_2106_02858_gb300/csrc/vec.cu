@@ -116,6 +116,41 @@ __device__ __forceinline__ double tet_dot(const R* X, const R* Y, int64_t tile, 
   return total;
 }
 
+// (X, Y) and (X, X) of one tetrahedron in one pass over X (each sum in the order of tet_dot).
+template <int Q, typename R>
+__device__ __forceinline__ void tet_dot2(const R* X, const R* Y, int64_t tile, int lane, const double* wdot,
+                                         double& xy, double& xx) {
+  constexpr int NP = np_of(Q);
+  const R* x = X + tile * (6 * NP * TILE) + lane;
+  const R* y = Y + tile * (6 * NP * TILE) + lane;
+  const double wE = wdot[(tile * 2 + 0) * TILE + lane], wH = wdot[(tile * 2 + 1) * TILE + lane];
+  xy = 0;
+  xx = 0;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    double xv[NP], yv[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      xv[j] = double(x[(c * NP + j) * TILE]);
+      yv[j] = double(y[(c * NP + j) * TILE]);
+    }
+    double s = 0, s2 = 0;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      double t = 0, t2 = 0;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) {
+        t = fma(cM<Q>(i * NP + j), yv[j], t);
+        t2 = fma(cM<Q>(i * NP + j), xv[j], t2);
+      }
+      s = fma(xv[i], t, s);
+      s2 = fma(xv[i], t2, s2);
+    }
+    xy += (c < 3 ? wE : wH) * s;
+    xx += (c < 3 ? wE : wH) * s2;
+  }
+}
+
 // Block b of the table: its tets, or -1 when past the block's range.
 __device__ __forceinline__ int64_t block_tet(const BlockTable& bt) {
   const int b = blockIdx.x;
@@ -137,8 +172,7 @@ __global__ void __launch_bounds__(DOT_THREADS) cg_after_adjoint_kernel(const R* 
     const int64_t base = tile * (6 * NP * TILE) + lane;
 #pragma unroll
     for (int k = 0; k < 6 * NP; ++k) A[base + k * TILE] = R(double(Uw[base + k * TILE]) - double(WT[base + k * TILE]));
-    acc = tet_dot<Q, R>(D, A, tile, lane, wdot);
-    dd = tet_dot<Q, R>(D, D, tile, lane, wdot);
+    tet_dot2<Q, R>(D, A, tile, lane, wdot, acc, dd);
   }
   const double s = block_sum(acc);
   const double s2 = block_sum(dd);

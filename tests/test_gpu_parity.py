@@ -264,3 +264,39 @@ def test_unstable_time_step_is_reported(lib, prec):
     e, hh, info = lib.cmcg_solve(h, p.j_re, p.j_im, 1e-6, 400)
     assert info.status == lib.CMCG_OK
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fw_baseline_matches_oracle(lib, prec):
+    """Limiting-amplitude baseline (Section 6): F_psi(P_psi^l 0) equals the oracle's for l = 0, 3."""
+    from oracle import fw as ofw
+    from oracle.timestep import Stepper
+    p = _problem("scatterer8", 2)
+    g = _geo(p)
+    st = Stepper(g, p.omega)
+    P = lib.CMCG_FP64 if prec == "fp64" else lib.CMCG_FP32
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    h, _ = lib.create_for_problem(p, precision=P)
+    for periods in (0, 3):
+        e, hh = lib.cmcg_fw_solve(h, p.j_re, p.j_im, periods)
+        ref = ofw.fw_solve(st, p.j_re, p.j_im, periods)
+        assert _rel(np.concatenate([e, hh], axis=1), ref, g) < tol, periods
+    h.close()
+
+
+def test_fw_batch_approaches_cmcg_and_matches_single(lib):
+    """On the open 3^3 cube FW approaches the CMCG result as the simulated periods grow (the
+    oracle gives 3.5e-2, 1.8e-4, 1.6e-7 at 2, 6, 12 periods); the batch entry equals the single."""
+    p = _problem("cube3", 1)
+    g = _geo(p)
+    h, _ = lib.create_for_problem(p, precision=lib.CMCG_FP64)
+    e_cg, h_cg, info = lib.cmcg_solve(h, p.j_re, p.j_im, 1e-10, 400)
+    ref = np.concatenate([e_cg, h_cg], axis=1)
+    errs = []
+    for periods in (2, 6, 12):
+        e, hh = lib.cmcg_fw_solve(h, p.j_re, p.j_im, periods)
+        errs.append(_rel(np.concatenate([e, hh], axis=1), ref, g))
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-6
+    eb, hb = lib.cmcg_fw_solve_batch(h, [p.j_re], [p.j_im], 12)
+    assert np.array_equal(eb[0], e) and np.array_equal(hb[0], hh)
+    h.close()
