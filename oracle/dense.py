@@ -56,12 +56,18 @@ def period_map(B: np.ndarray, dt: float, M: int, integrator: str) -> np.ndarray:
     return np.linalg.matrix_power(amplification(B, dt, integrator), M)
 
 
-def frequency_solve(geo, omega: float, j_re, j_im=None) -> np.ndarray:
-    """FS: (i w I - B) U = J with J = (j_re + i j_im)/eps on the E rows."""
+def frequency_solve(geo, omega: float, j_re, j_im=None, g_re=None, g_im=None) -> np.ndarray:
+    """FS: (i w I - B) U = J + b with J = (j_re + i j_im)/eps on the E rows and b the
+    (complex) boundary-data term of g = g_re + i g_im on impedance faces."""
     B = dense_B(geo)
     Jr = source_term(0.0, omega, j_re, j_im, geo)  # Re part of J at t = 0 is j_re / eps
     Ji = -source_term(np.pi / (2 * omega), omega, j_re, j_im, geo) if j_im is not None else np.zeros_like(Jr)
     # at t = pi/(2w): Re(J e^{i pi/2}) = -Im J  ->  Im J = -source_term(...)
+    if g_re is not None:  # b(g) = B_g(0, g) is linear in g: real and imaginary parts separately
+        zero = np.zeros_like(Jr)
+        Jr = Jr + apply_B(zero, geo, G=np.asarray(g_re))
+        if g_im is not None:
+            Ji = Ji + apply_B(zero, geo, G=np.asarray(g_im))
     J = (Jr + 1j * Ji).reshape(-1)
     n = B.shape[0]
     U = np.linalg.solve(1j * omega * np.eye(n) - B, J)

@@ -19,6 +19,13 @@ and the boundary traces
   PEC:        E^ = 0,                       H^ = H^- + Y E^- x n
   impedance:  E^ = (E^- - Z H^- x n) / 2,   H^ = (H^- + Y E^- x n) / 2.
 
+Boundary data on impedance faces (the incident-field datum of Section 5.2.2's
+impedance traces): the exterior state of the upwind flux is (E^+, H^+) =
+(g(t), 0) with Z^+ = Z^-, i.e. the impedance traces gain g / 2 in E^ and
+Y n x g / 2 in H^.  An incident field (E_i, H_i) of the boundary medium is
+reproduced exactly by g = E_i - Z n x H_i: its traces then coincide with the
+interior upwind traces against (E_i, H_i).
+
 The jump signs are the ones that make the scheme dissipative and the
 impedance face transparent to outgoing plane waves (the paper's 2D signs are
 not consistent with its own PDE).  ``flux="centred"`` drops the jump terms
@@ -66,9 +73,10 @@ def _cross(n: np.ndarray, v: np.ndarray) -> np.ndarray:
                      n[..., 0, :] * v[..., 1, :] - n[..., 1, :] * v[..., 0, :]], axis=-2)
 
 
-def numerical_traces(U: np.ndarray, geo: Geometry, flux: str = "upwind"):
+def numerical_traces(U: np.ndarray, geo: Geometry, flux: str = "upwind", G=None):
     """Own traces (E^-, H^-) and numerical traces (E^, H^) on every face node.
 
+    G: boundary data (nt, 4, 3, Nfp) at this time, read on impedance faces only (None = 0).
     Returns (n, Em, Hm, Ehat, Hhat), each (..., nt, 4, 3, Nfp) (n without the batch axes)."""
     R = ref_element(geo.q)
     nt = geo.nt
@@ -106,19 +114,24 @@ def numerical_traces(U: np.ndarray, geo: Geometry, flux: str = "upwind"):
         H_imp = 0.5 * Hm
     else:
         raise ValueError(flux)
+    if G is not None:  # exterior state (G, 0) on impedance faces
+        E_imp = E_imp + 0.5 * G
+        if flux == "upwind":
+            H_imp = H_imp + 0.5 * Ym * _cross(n, G)
     Ehat = np.where(interior, E_int, np.where(pec, E_pec, E_imp))
     Hhat = np.where(interior, H_int, np.where(pec, H_pec, H_imp))
     return n, Em, Hm, Ehat, Hhat
 
 
-def apply_B(U: np.ndarray, geo: Geometry, adjoint: bool = False, flux: str = "upwind") -> np.ndarray:
-    """B U (or Sigma B Sigma U when ``adjoint``), the source-free part of Phi."""
+def apply_B(U: np.ndarray, geo: Geometry, adjoint: bool = False, flux: str = "upwind", G=None) -> np.ndarray:
+    """B U (or Sigma B Sigma U when ``adjoint``), the source-free part of Phi; with boundary data
+    G (see numerical_traces) the affine map B U + b(G)."""
     if adjoint:
         return sigma(apply_B(sigma(U), geo, adjoint=False, flux=flux))
     R = ref_element(geo.q)
     E, H = U[..., :3, :], U[..., 3:, :]
     curlE, curlH = _curl(E, geo), _curl(H, geo)
-    n, Em, Hm, Ehat, Hhat = numerical_traces(U, geo, flux)
+    n, Em, Hm, Ehat, Hhat = numerical_traces(U, geo, flux, G)
     fE = _cross(n, Hhat - Hm)  # n x (H^ - H^-), enters the E equation with a minus sign
     fH = _cross(n, Ehat - Em)  # n x (E^ - E^-), enters the H equation with a plus sign
     scale = (geo.sJ / geo.J[:, None])[:, :, None, None]  # (nt, 4, 1, 1): face Jacobian / volume Jacobian
@@ -142,9 +155,19 @@ def source_term(t: float, omega: float, j_re: np.ndarray, j_im: np.ndarray, geo:
     return out
 
 
-def Phi(t: float, U: np.ndarray, geo: Geometry, omega: float, j_re=None, j_im=None, flux: str = "upwind") -> np.ndarray:
-    """Phi(t, U) = Re(J e^{i w t}) + B U (Eq. ode_system)."""
-    out = apply_B(U, geo, flux=flux)
+def boundary_data(t: float, omega: float, g_re, g_im) -> np.ndarray:
+    """g(t) = Re((g_re + i g_im) e^{i w t}) at the face nodes, (nt, 4, 3, Nfp)."""
+    gr = np.asarray(g_re)
+    gi = np.zeros_like(gr) if g_im is None else np.asarray(g_im)
+    return gr * np.cos(omega * t) - gi * np.sin(omega * t)
+
+
+def Phi(t: float, U: np.ndarray, geo: Geometry, omega: float, j_re=None, j_im=None, flux: str = "upwind",
+        g_re=None, g_im=None) -> np.ndarray:
+    """Phi(t, U) = Re(J e^{i w t}) + B U (Eq. ode_system), with the impedance-face data
+    Re(g e^{i w t}) in the traces when g_re is given."""
+    G = None if g_re is None else boundary_data(t, omega, g_re, g_im)
+    out = apply_B(U, geo, flux=flux, G=G)
     if j_re is not None:
         out = out + source_term(t, omega, j_re, j_im, geo)
     return out

@@ -52,8 +52,10 @@ class Stepper:
     """The fully discrete scheme of one problem: geometry, w, integrator, M, dt."""
 
     def __init__(self, geo: Geometry, omega: float, c_q: Optional[float] = None, M: Optional[int] = None,
-                 flux: str = "upwind", integrator: Optional[str] = None):
+                 flux: str = "upwind", integrator: Optional[str] = None, g_re=None, g_im=None):
+        """g_re, g_im: impedance-face data (nt, 4, 3, Nfp) of the source sweeps (None: none)."""
         self.geo = geo
+        self.g_re, self.g_im = g_re, g_im
         self.omega = omega
         self.T = 2.0 * math.pi / omega
         self.M = steps_per_period(geo, omega, c_q) if M is None else M
@@ -65,7 +67,10 @@ class Stepper:
     def phi(self, j_re=None, j_im=None, adjoint: bool = False) -> Callable:
         if adjoint:
             return lambda t, U: apply_B(U, self.geo, adjoint=True, flux=self.flux)
-        return lambda t, U: Phi(t, U, self.geo, self.omega, j_re, j_im, flux=self.flux)
+        if j_re is None:  # source-free sweep: the linear map B (no boundary data either)
+            return lambda t, U: Phi(t, U, self.geo, self.omega, None, None, flux=self.flux)
+        return lambda t, U: Phi(t, U, self.geo, self.omega, j_re, j_im, flux=self.flux, g_re=self.g_re,
+                                g_im=self.g_im)
 
     def sweep(self, U0: np.ndarray, j_re=None, j_im=None, adjoint: bool = False, callback=None) -> np.ndarray:
         """March M steps from t = 0; ``callback(m, U_m, K1_m)`` sees every step's start state."""
