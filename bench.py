@@ -300,6 +300,23 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     nj = prob.nt * 3 * prob.np_ * 8
     h2d, d2h = 2 * nj, 4 * nj
 
+    # The paper's comparison method at equal cost: the limiting-amplitude iteration (FW) run for
+    # as many periods as one CMCG solve simulates, and its distance from the CMCG result.
+    fw = None
+    if not args.skip_fw:
+        fw_periods = 3 + 2 * infos[-1].iters - 1  # FW simulates periods + 1
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        efw, hfw = cmcg.cmcg_fw_solve(h32, jr_h, ji_h, fw_periods)
+        fw_s = time.perf_counter() - t0
+        ecg, hcg = e32[0] + 1j * e32[1], e32[2] + 1j * e32[3]
+        fwf = np.concatenate([efw, hfw], axis=1)
+        cgf = np.concatenate([ecg, hcg], axis=1)
+        d = fwf - cgf
+        num = cmcg.cmcg_inner(h32, d.real, d.real) + cmcg.cmcg_inner(h32, d.imag, d.imag)
+        den = cmcg.cmcg_inner(h32, cgf.real, cgf.real) + cmcg.cmcg_inner(h32, cgf.imag, cgf.imag)
+        fw = {"periods": fw_periods + 1, "seconds": fw_s, "rel_l2_vs_cmcg": math.sqrt(num / den)}
+
     # FP64 plain solve of the same problem: accuracy of the FP32 result and the FP64 rate.
     fp64 = None
     if not args.skip_fp64:
@@ -368,6 +385,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "gpu_launches": int(launches),
             "roofline": roofline,
             "clocks": clocks,
+            "fw_at_equal_periods": fw,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -403,6 +421,7 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fw", action="store_true")
     ap.add_argument("--profile-sweep", action="store_true", help="run one period sweep only (for ncu)")
     ap.add_argument("--stage-variant", type=int, default=0, help="force a stage-kernel form (see cmcg_options)")
     args = ap.parse_args()

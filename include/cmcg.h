@@ -311,6 +311,20 @@ int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, do
  * counter kept on the host at every launch). */
 int64_t cmcg_kernel_launches(const cmcg_handle* h);
 
+/* Impedance-face data g (the incident-field datum of the impedance traces,
+ * Section 5.2.2) for problem `problem` of the handle: on every impedance face
+ * the upwind flux sees the exterior state (E+, H+) = (Re(g e^{i w t}), 0) with
+ * the boundary tetrahedron's own Z.  An incident field (E_i, H_i) of that
+ * medium is passed exactly by g = E_i - Z n x H_i (n the outward normal).
+ * g_re, g_im: host double[nt][4][3][Nfp] (tetrahedron, face opposite vertex f,
+ * component x y z, face node in increasing volume-node order); read on
+ * impedance faces only; g_im may be NULL (= 0); g_re NULL clears the data.
+ * The data enter every sweep that carries the source j (cmcg_solve,
+ * cmcg_fw_solve, dgtd_period_forward and dgtd_apply with j given; pass j = 0
+ * for a problem driven by g alone) and stay until cleared or replaced.  The
+ * first call allocates two field vectors on the device. */
+int cmcg_set_boundary_data(cmcg_handle* h, int problem, const double* g_re, const double* g_im);
+
 /* Limiting-amplitude baseline ("full wave", FW, Section 6): marches the
  * scheme with the time-harmonic source from rest for `periods` periods,
  * U = P_{psi,w}^periods 0, then returns the filtered field F_{psi,w} U of one

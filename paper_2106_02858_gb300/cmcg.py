@@ -99,6 +99,7 @@ def _load() -> C.CDLL:
                                          C.POINTER(cmcg_info)]),
         "cmcg_device_bytes": (C.c_int64, [_vp]),
         "cmcg_fw_solve": (C.c_int, [_vp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]),
+        "cmcg_set_boundary_data": (C.c_int, [_vp, C.c_int, _dp, _dp]),
         "cmcg_fw_solve_batch": (C.c_int, [_vp, C.c_int, C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp),
                                           C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp)]),
         "cmcg_server_default_options": (None, [C.POINTER(cmcg_server_options)]),
@@ -144,7 +145,7 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_solve_device", "cmcg_kernel_launches", "cmcg_profile_enable", "cmcg_profile_read",
             "cmcg_inner", "cmcg_inner_noalloc", "cmcg_get_tuning", "cmcg_create_batch", "cmcg_batch_size",
             "cmcg_get_problem", "cmcg_solve_batch", "cmcg_solve_batch_device", "cmcg_solve_batch_n",
-            "cmcg_device_bytes", "cmcg_fw_solve", "cmcg_fw_solve_batch", "cmcg_server_default_options", "cmcg_server_create", "cmcg_server_add_model",
+            "cmcg_device_bytes", "cmcg_fw_solve", "cmcg_fw_solve_batch", "cmcg_set_boundary_data", "cmcg_server_default_options", "cmcg_server_create", "cmcg_server_add_model",
             "cmcg_server_submit", "cmcg_server_poll", "cmcg_server_stats", "cmcg_server_destroy")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
@@ -450,6 +451,16 @@ def cmcg_solve(h: Handle, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 10
     _check(_lib.cmcg_solve(h.ptr, _ptr(jr), _ptr(ji), float(tol), int(max_iter), _ptr(er), _ptr(ei), _ptr(hr),
                            _ptr(hi), C.byref(info)), "cmcg_solve", allow_not_converged=True)
     return er + 1j * ei, hr + 1j * hi, info
+
+
+def cmcg_set_boundary_data(h: Handle, g_re, g_im=None, problem: int = 0) -> None:
+    """Impedance-face data g, arrays (nt, 4, 3, Nfp) of problem `problem`; g_re None clears."""
+    nt = h.problems[problem][0]
+    nfp = {4: 3, 10: 6, 20: 10}[h.np]
+    gr = None if g_re is None else _f64(g_re, (nt, 4, 3, nfp), "g_re")
+    gi = None if (g_re is None or g_im is None) else _f64(g_im, (nt, 4, 3, nfp), "g_im")
+    h._keep_b = (gr, gi)
+    _check(_lib.cmcg_set_boundary_data(h.ptr, int(problem), _ptr(gr), _ptr(gi)), "cmcg_set_boundary_data")
 
 
 def cmcg_fw_solve(h: Handle, j_re, j_im=None, periods: int = 1):

@@ -37,6 +37,15 @@ using namespace cmcg;
 
 namespace {
 
+// An impedance face of a problem: what its boundary data need on the host.
+struct ImpFace {
+  int64_t it = 0;        // internal tetrahedron (handle-wide index)
+  int32_t ext = 0;       // external tetrahedron within its problem
+  int f = 0;             // face
+  double n[3] = {0, 0, 0};
+  double aE = 0, bH = 0;  // flux coefficients of the E rows (tangential jump) and H rows (n x jump)
+};
+
 struct Prob {
   int64_t nt = 0;                     // external tetrahedra
   int64_t tet0 = 0, nti = 0;          // internal range
@@ -45,6 +54,8 @@ struct Prob {
   int M = 0;
   double dt = 0, T = 0, omega = 0;
   std::vector<std::complex<double>> fa, fb;  // filter weights per step 0..M (with 2/T)
+  std::vector<ImpFace> imp;                   // impedance faces
+  bool has_bdata = false;                     // boundary data set (cmcg_set_boundary_data)
 };
 
 }  // namespace
@@ -67,6 +78,7 @@ struct cmcg_handle {
   // vectors
   void *Uw = nullptr, *vA = nullptr, *vB = nullptr, *ACC = nullptr, *Fre = nullptr, *Fim = nullptr;
   void *Jre = nullptr, *Jim = nullptr;
+  void *Bre = nullptr, *Bim = nullptr;  // lifted impedance-face data, all 6 rows (allocated on first use)
   void *U0 = nullptr, *Rv = nullptr, *D = nullptr, *A = nullptr, *WT = nullptr;
   // CG
   double* partials = nullptr;
@@ -86,6 +98,7 @@ struct cmcg_handle {
   double *ext0 = nullptr, *ext1 = nullptr, *ext2 = nullptr, *ext3 = nullptr;
   int64_t launches = 0;
   size_t bytes = 0;
+  bool has_bdata = false;  // some problem has boundary data
   int form = 0;      // stage-kernel form (see launch_stage)
   bool pdl = false;  // stages launched with programmatic stream serialisation
   double tune_us[8];
@@ -359,6 +372,10 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
     if (with_source) {
       a.jre = (const R*)h->Jre;
       a.jim = (const R*)h->Jim;
+      if (h->has_bdata) {
+        a.bre = (const R*)h->Bre;
+        a.bim = (const R*)h->Bim;
+      }
     }
     if (filter && r == 0) {
       a.fre = (R*)h->Fre;
@@ -540,6 +557,10 @@ int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, con
     if (rc) return rc;
     a.jre = (const R*)h->Jre;
     a.jim = (const R*)h->Jim;
+    if (h->has_bdata) {
+      a.bre = (const R*)h->Bre;
+      a.bim = (const R*)h->Bim;
+    }
   }
   stage<R>(h, a);
   to_ext<R>(h, 0, h->vA, 6, 0, out, 6, 6);
@@ -687,7 +708,7 @@ int fw_dev(cmcg_handle* h, int periods, const double* const* j_re, const double*
 
 void free_all(cmcg_handle* h) {
   void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
-                  h->Fre, h->Fim, h->Jre, h->Jim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
+                  h->Fre, h->Fim, h->Jre, h->Jim, h->Bre, h->Bim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
                   h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
                   h->ext0, h->ext1, h->ext2, h->ext3, h->used};
   for (void* p : ptrs)
@@ -764,6 +785,20 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
       wdot.insert(wdot.end(), L.wdot.begin(), L.wdot.end());
       const int32_t shift = int32_t(P.tet0) << 5;
       for (int32_t c : L.nbr) nbr.push_back(c >= 0 ? c + shift : c);
+      for (int64_t t = 0; t < L.ntiles; ++t)
+        for (int f = 0; f < 4; ++f)
+          for (int l = 0; l < TILE; ++l) {
+            if (L.nbr[(t * 4 + f) * TILE + l] != NBR_IMP || L.ext_of_int[t * TILE + l] < 0) continue;
+            ImpFace F;
+            F.it = P.tet0 + t * TILE + l;
+            F.ext = L.ext_of_int[t * TILE + l];
+            F.f = f;
+            auto gf = [&](int item) { return L.gface[((t * 4 + f) * GF + item) * TILE + l]; };
+            for (int a = 0; a < 3; ++a) F.n[a] = gf(a);
+            F.bH = gf(3);
+            F.aE = gf(6);
+            P.imp.push_back(F);
+          }
       e_of_i.insert(e_of_i.end(), L.ext_of_int.begin(), L.ext_of_int.end());
       for (int64_t t = 0; t < L.ntiles; ++t) tprob.push_back(p);
       for (int64_t k = 0; k < L.nt; ++k) inv_eps.push_back(1.0 / probs[p].eps[k]);
@@ -1190,6 +1225,88 @@ int cmcg_solve_batch_n(cmcg_handle* h, int n, const double* const* j_re, const d
   if (rc < 0) return rc;
   const int rc2 = copy_host_outputs(h, n, io, e_re, e_im, h_re, h_im);
   return rc2 ? rc2 : rc;
+}
+
+int cmcg_set_boundary_data(cmcg_handle* h, int problem, const double* g_re, const double* g_im) {
+  if (!h || problem < 0 || problem >= h->nprob) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  Prob& P = h->P[problem];
+  const int np = h->np, nfp = nfp_of(h->q);
+  const size_t R_ = h->rsize;
+  const size_t off = size_t(P.tet0) * 6 * np, cnt = size_t(P.nti) * 6 * np;  // the problem's tiles
+  if (!g_re) {  // clear
+    if (h->Bre) {
+      CK(cudaMemsetAsync(static_cast<char*>(h->Bre) + off * R_, 0, cnt * R_, h->stream));
+      CK(cudaMemsetAsync(static_cast<char*>(h->Bim) + off * R_, 0, cnt * R_, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    P.has_bdata = false;
+  } else {
+    if (!h->Bre) {
+      const size_t bytes = size_t(h->nvec) * R_;
+      if (cudaMalloc(&h->Bre, bytes) != cudaSuccess) return CMCG_ERR_OUT_OF_MEMORY;
+      if (cudaMalloc(&h->Bim, bytes) != cudaSuccess) {
+        cudaFree(h->Bre);
+        h->Bre = nullptr;
+        return CMCG_ERR_OUT_OF_MEMORY;
+      }
+      h->bytes += 2 * bytes;
+      CK(cudaMemsetAsync(h->Bre, 0, bytes, h->stream));
+      CK(cudaMemsetAsync(h->Bim, 0, bytes, h->stream));
+    }
+    // The data term of Phi is linear in g: with the exterior state (g, 0) the flux of a face gains
+    // aE (g - n (n.g)) on the E rows and bH n x g on the H rows, lifted like every flux.  Summed
+    // here once per call in double precision, in the field layout of the problem's tiles.
+    const RefMats& rm = ref_mats(h->q);
+    std::vector<double> hre(cnt, 0.0), him(cnt, 0.0);
+    for (const ImpFace& F : P.imp) {
+      const int64_t li = F.it - P.tet0, tile = li / TILE, lane = li % TILE;
+      for (int jf = 0; jf < nfp; ++jf) {
+        double fE[2][3], fH[2][3];
+        for (int part = 0; part < 2; ++part) {
+          const double* g = part ? g_im : g_re;
+          double gv[3] = {0, 0, 0};
+          if (g)
+            for (int c = 0; c < 3; ++c) gv[c] = g[((size_t(F.ext) * 4 + F.f) * 3 + c) * nfp + jf];
+          const double ng = F.n[0] * gv[0] + F.n[1] * gv[1] + F.n[2] * gv[2];
+          const double nxg[3] = {F.n[1] * gv[2] - F.n[2] * gv[1], F.n[2] * gv[0] - F.n[0] * gv[2],
+                                 F.n[0] * gv[1] - F.n[1] * gv[0]};
+          for (int c = 0; c < 3; ++c) {
+            fE[part][c] = F.aE * (gv[c] - F.n[c] * ng);
+            fH[part][c] = F.bH * nxg[c];
+          }
+        }
+        for (int i = 0; i < np; ++i) {
+          const double L = rm.LIFT[size_t(i) * 4 * nfp + F.f * nfp + jf];
+          for (int c = 0; c < 3; ++c) {
+            const size_t oE = size_t(tile) * 6 * np * TILE + size_t(c * np + i) * TILE + lane;
+            const size_t oH = size_t(tile) * 6 * np * TILE + size_t((3 + c) * np + i) * TILE + lane;
+            hre[oE] += L * fE[0][c];
+            him[oE] += L * fE[1][c];
+            hre[oH] += L * fH[0][c];
+            him[oH] += L * fH[1][c];
+          }
+        }
+      }
+    }
+    // copies ordered after the zeroing above on the handle's stream; host buffers live until the sync
+    if (h->prec == CMCG_FP32) {
+      std::vector<float> fre(hre.begin(), hre.end()), fim(him.begin(), him.end());
+      CK(cudaMemcpyAsync(static_cast<float*>(h->Bre) + off, fre.data(), cnt * 4, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaMemcpyAsync(static_cast<float*>(h->Bim) + off, fim.data(), cnt * 4, cudaMemcpyHostToDevice, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    } else {
+      CK(cudaMemcpyAsync(static_cast<double*>(h->Bre) + off, hre.data(), cnt * 8, cudaMemcpyHostToDevice,
+                         h->stream));
+      CK(cudaMemcpyAsync(static_cast<double*>(h->Bim) + off, him.data(), cnt * 8, cudaMemcpyHostToDevice,
+                         h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+    }
+    P.has_bdata = true;
+  }
+  h->has_bdata = false;
+  for (const Prob& Q : h->P) h->has_bdata = h->has_bdata || Q.has_bdata;
+  return CMCG_OK;
 }
 
 int cmcg_fw_solve_batch(cmcg_handle* h, int periods, const double* const* j_re, const double* const* j_im,

@@ -91,7 +91,7 @@ constexpr int32_t NBR_IMP = -2;
 
 // Per-problem coefficients of one stage launch (a handle holds a batch of
 // problems that advance in lockstep; each reads its own entry).
-//   Phi   = src + B_sigma(vin),  src = s_cos * jre - s_sin * jim   (B_sigma = Sigma B Sigma when sH = -1)
+//   Phi   = src + B_sigma(vin),  src = s_cos * (jre + bre) - s_sin * (jim + bim)   (B_sigma = Sigma B Sigma when sH = -1)
 //   out   = base + c_out Phi        (skipped if out == nullptr)
 //   acc_o = acc_i + c_acc Phi       (skipped if acc_o == nullptr)
 //   F    += fa vin + fb Phi         (complex weights; skipped if fre == nullptr)
@@ -112,6 +112,8 @@ struct StageArgs {
   R* acc_out;
   const R* jre;  // E-rows source / eps, [tile][3][Np][32] (null: no source)
   const R* jim;
+  const R* bre;  // lifted impedance-face data, all 6 rows in the field layout (null: none)
+  const R* bim;
   R* fre;        // filter accumulators (null: no filter)
   R* fim;
   R sH;          // +1 forward, -1 adjoint

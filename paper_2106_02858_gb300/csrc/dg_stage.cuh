@@ -201,6 +201,10 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
   }
 
   cp_async_wait_all();
+  // The face term in two passes: first every face node's flux (24 independent
+  // chains of trace read, jump, partner shuffle and flux, stored over the trace
+  // slots the thread owns), then the lift as a stream of FMAs.  The values and
+  // the order of the lift sums are those of a single pass.
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     const R n0 = fn[f][0], n1 = fn[f][1], n2 = fn[f][2];
@@ -221,10 +225,19 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
 #pragma unroll
       for (int c = 0; c < 3; ++c) Y[c] = __shfl_xor_sync(0xffffffffu, X[c], 1);
       const R nY = n0 * Y[0] + n1 * Y[1] + n2 * Y[2];
+      tr[((f * NFP + jf) * 3 + 0) * STAGE_THREADS] = k1 * (n1 * X[2] - n2 * X[1]) + k2 * (Y[0] - n0 * nY);
+      tr[((f * NFP + jf) * 3 + 1) * STAGE_THREADS] = k1 * (n2 * X[0] - n0 * X[2]) + k2 * (Y[1] - n1 * nY);
+      tr[((f * NFP + jf) * 3 + 2) * STAGE_THREADS] = k1 * (n0 * X[1] - n1 * X[0]) + k2 * (Y[2] - n2 * nY);
+    }
+  }
+  // pass 2: the lift
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+#pragma unroll
+    for (int jf = 0; jf < NFP; ++jf) {
       R fl[3];
-      fl[0] = k1 * (n1 * X[2] - n2 * X[1]) + k2 * (Y[0] - n0 * nY);
-      fl[1] = k1 * (n2 * X[0] - n0 * X[2]) + k2 * (Y[1] - n1 * nY);
-      fl[2] = k1 * (n0 * X[1] - n1 * X[0]) + k2 * (Y[2] - n2 * nY);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) fl[c] = tr[((f * NFP + jf) * 3 + c) * STAGE_THREADS];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         const R L = cL<R>(i * 4 * NFP + f * NFP + jf);
@@ -242,6 +255,15 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
       for (int n = 0; n < NP; ++n) {
         const int64_t o = joff + (c * NP + n) * TILE;
         phi[c][n] += cf.s_cos * a.jre[o] - cf.s_sin * a.jim[o];
+      }
+  }
+  if (a.bre) {  // impedance-face data, lifted onto this thread's output rows (source sweeps only)
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        const int64_t o = off + (c * NP + n) * TILE;
+        phi[c][n] += cf.s_cos * a.bre[o] - cf.s_sin * a.bim[o];
       }
   }
   if (a.fre) {  // forward sweeps only: F += fa U + fb Phi on this thread's output rows
@@ -489,6 +511,15 @@ __device__ __forceinline__ void quad_stage(const StageArgs<R>& a) {
       for (int ii = 0; ii < NH; ++ii) {
         const int64_t o = joff + (c * NP + I0 + ii) * TILE;
         phi[c][ii] += cf.s_cos * a.jre[o] - cf.s_sin * a.jim[o];
+      }
+  }
+  if (a.bre) {  // impedance-face data on this thread's output rows
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int ii = 0; ii < NH; ++ii) {
+        const int64_t o = off + (c * NP + I0 + ii) * TILE;
+        phi[c][ii] += cf.s_cos * a.bre[o] - cf.s_sin * a.bim[o];
       }
   }
   if (a.fre) {
