@@ -120,7 +120,12 @@ typedef struct cmcg_mesh {
  *                     the form is forced); 1 = on; 2 = off.  On: each stage
  *                     is launched with programmatic stream serialisation, so
  *                     its blocks start and load the mesh data while the
- *                     previous stage finishes.  Results are identical. */
+ *                     previous stage finishes.  Results are identical.
+ *   launch_graphs:    0 or 1 = each period sweep (its stage launches) is
+ *                     captured once as a CUDA graph on a private stream and
+ *                     replayed on the handle's stream; 2 = direct launches.
+ *                     If the driver refuses the capture, the handle falls
+ *                     back to direct launches.  Results are identical. */
 typedef struct cmcg_options {
   int order;
   int precision;
@@ -131,7 +136,8 @@ typedef struct cmcg_options {
   int device;
   int stage_variant;
   int stage_overlap;
-  int reserved[5];
+  int launch_graphs;
+  int reserved[4];
 } cmcg_options;
 
 /* Per-solve report. */

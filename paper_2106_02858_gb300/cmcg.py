@@ -43,7 +43,8 @@ class cmcg_mesh(C.Structure):
 class cmcg_options(C.Structure):
     _fields_ = [("order", C.c_int), ("precision", C.c_int), ("flux", C.c_int), ("steps_per_period", C.c_int),
                 ("c_q", C.c_double), ("hbm_budget_bytes", C.c_int64), ("device", C.c_int),
-                ("stage_variant", C.c_int), ("stage_overlap", C.c_int), ("reserved", C.c_int * 5)]
+                ("stage_variant", C.c_int), ("stage_overlap", C.c_int), ("launch_graphs", C.c_int),
+                ("reserved", C.c_int * 4)]
 
 
 class cmcg_info(C.Structure):
@@ -188,12 +189,14 @@ def _check(rc: int, where: str, allow_not_converged: bool = False) -> int:
 
 def cmcg_default_options(order: int = 1, precision: int = CMCG_FP64, flux: int = CMCG_FLUX_UPWIND,
                          steps_per_period: int = 0, c_q: float = 0.0, hbm_budget_bytes: int = 0,
-                         device: int = 0, stage_variant: int = 0, stage_overlap: int = 0) -> cmcg_options:
+                         device: int = 0, stage_variant: int = 0, stage_overlap: int = 0,
+                         launch_graphs: int = 0) -> cmcg_options:
     o = cmcg_options()
     _lib.cmcg_default_options(C.byref(o))
     o.order, o.precision, o.flux, o.steps_per_period = order, precision, flux, steps_per_period
     o.c_q, o.hbm_budget_bytes, o.device, o.stage_variant = c_q, hbm_budget_bytes, device, stage_variant
     o.stage_overlap = stage_overlap
+    o.launch_graphs = launch_graphs
     return o
 
 
@@ -495,12 +498,14 @@ def cmcg_solve_device(h: Handle, j_re, j_im, tol: float, max_iter: int, e_re, e_
 
 
 def create_for_problem(problem, precision: int = CMCG_FP64, flux: int = CMCG_FLUX_UPWIND, steps_per_period: int = 0,
-                       device: int = 0, hbm_budget_bytes: int = 0, stage_variant: int = 0, stage_overlap: int = 0):
+                       device: int = 0, hbm_budget_bytes: int = 0, stage_variant: int = 0, stage_overlap: int = 0,
+                       launch_graphs: int = 0):
     """Convenience: cmcg_create from an ``inputs.Problem``; returns (handle, mesh arrays)."""
     mesh = make_mesh(problem.mesh.verts, problem.mesh.tets, problem.mesh.tags)
     opt = cmcg_default_options(order=problem.order, precision=precision, flux=flux,
                                steps_per_period=steps_per_period, device=device, hbm_budget_bytes=hbm_budget_bytes,
-                               stage_variant=stage_variant, stage_overlap=stage_overlap)
+                               stage_variant=stage_variant, stage_overlap=stage_overlap,
+                               launch_graphs=launch_graphs)
     return cmcg_create(mesh, problem.eps, problem.mu, problem.omega, opt), mesh
 
 

@@ -28,8 +28,10 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 
 #include "common.h"
 
@@ -99,6 +101,11 @@ struct cmcg_handle {
   int64_t launches = 0;
   size_t bytes = 0;
   bool has_bdata = false;  // some problem has boundary data
+  // CUDA graphs of whole sweeps, captured on first use on a private stream and launched on
+  // `stream`; key: sweep kind, mask pointer, boundary data present.
+  bool graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  std::map<std::tuple<int, const void*, bool>, cudaGraphExec_t> graph_exec;
   int form = 0;      // stage-kernel form (see launch_stage)
   bool pdl = false;  // stages launched with programmatic stream serialisation
   double tune_us[8];
@@ -266,16 +273,54 @@ const StageCoef<R>* tab(void* t, int l, int nprob) {
 }
 
 template <typename R>
-void stage(cmcg_handle* h, StageArgs<R>& a) {
+void stage(cmcg_handle* h, StageArgs<R>& a, cudaStream_t st) {
   a.gvol = (const R*)h->gvol;
   a.gface = (const R*)h->gface;
   a.nbr = h->nbr;
   a.nti = h->nti;
   a.tprob = h->tprob;
-  if (h->q == 1) launch_stage<1, R>(a, h->stream, h->form, h->pdl);
-  else if (h->q == 2) launch_stage<2, R>(a, h->stream, h->form, h->pdl);
-  else launch_stage<3, R>(a, h->stream, h->form, h->pdl);
+  if (h->q == 1) launch_stage<1, R>(a, st, h->form, h->pdl);
+  else if (h->q == 2) launch_stage<2, R>(a, st, h->form, h->pdl);
+  else launch_stage<3, R>(a, st, h->form, h->pdl);
+}
+template <typename R>
+void stage(cmcg_handle* h, StageArgs<R>& a) {
+  stage<R>(h, a, h->stream);
   h->launches++;
+}
+
+// Runs `emit(stream)` (a fixed sequence of `n` stage launches) on the handle's stream, from a
+// CUDA graph captured at its first use under `key`; if capture or instantiation is refused,
+// the handle stops using graphs and launches directly.
+template <typename F>
+void run_sweep(cmcg_handle* h, std::tuple<int, const void*, bool> key, int n, F&& emit) {
+  if (h->graphs) {
+    auto it = h->graph_exec.find(key);
+    if (it == h->graph_exec.end()) {
+      cudaGraphExec_t exec = nullptr;
+      bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        emit(h->cap_stream);
+        cudaGraph_t g = nullptr;
+        ok = cudaStreamEndCapture(h->cap_stream, &g) == cudaSuccess && g;
+        if (ok) ok = cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+      }
+      if (!ok) {
+        cudaGetLastError();  // clear the refusal; fall back to direct launches
+        h->graphs = false;
+      } else {
+        it = h->graph_exec.emplace(key, exec).first;
+      }
+    }
+    if (h->graphs) {
+      cudaGraphLaunch(it->second, h->stream);
+      h->launches += n;
+      return;
+    }
+  }
+  emit(h->stream);
+  h->launches += n;
 }
 
 template <typename R>
@@ -326,17 +371,19 @@ void sweep_free(cmcg_handle* h, bool adjoint, const int32_t* pactive) {
   R* vA = (R*)h->vA;
   R* vB = (R*)h->vB;
   const int s = h->s;
-  for (int l = 0; l < h->L_free; ++l) {
-    const int r = l % s;
-    StageArgs<R> a = blank<R>();
-    a.vin = r == 0 ? Uw : (r % 2 == 1 ? vA : vB);
-    a.base = Uw;
-    a.out = r == s - 1 ? Uw : (r % 2 == 0 ? vA : vB);
-    a.sH = adjoint ? R(-1) : R(1);
-    a.coef = tab<R>(h->tab_free, l, h->nprob);
-    a.pactive = pactive;
-    stage<R>(h, a);
-  }
+  run_sweep(h, std::make_tuple(adjoint ? 1 : 0, (const void*)pactive, false), h->L_free, [&](cudaStream_t st) {
+    for (int l = 0; l < h->L_free; ++l) {
+      const int r = l % s;
+      StageArgs<R> a = blank<R>();
+      a.vin = r == 0 ? Uw : (r % 2 == 1 ? vA : vB);
+      a.base = Uw;
+      a.out = r == s - 1 ? Uw : (r % 2 == 0 ? vA : vB);
+      a.sH = adjoint ? R(-1) : R(1);
+      a.coef = tab<R>(h->tab_free, l, h->nprob);
+      a.pactive = pactive;
+      stage<R>(h, a, st);
+    }
+  });
   prof_end(h, pe);
 }
 
@@ -352,6 +399,8 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
   const int s = h->s;
   const int L = filter ? h->L_srcf : h->L_src;
   void* table = filter ? h->tab_srcf : h->tab_src;
+  const int kind = 2 + (filter ? 1 : 0) + (with_source ? 0 : 2);
+  run_sweep(h, std::make_tuple(kind, (const void*)mask, with_source && h->has_bdata), L, [&](cudaStream_t st) {
   for (int l = 0; l < L; ++l) {
     const int r = l % s;
     StageArgs<R> a = blank<R>();
@@ -383,8 +432,9 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
     }
     a.coef = tab<R>(table, l, h->nprob);
     a.pactive = mask;
-    stage<R>(h, a);
+    stage<R>(h, a, st);
   }
+  });
   prof_end(h, pe);
 }
 
@@ -707,6 +757,10 @@ int fw_dev(cmcg_handle* h, int periods, const double* const* j_re, const double*
 }
 
 void free_all(cmcg_handle* h) {
+  for (auto& kv : h->graph_exec) cudaGraphExecDestroy(kv.second);
+  h->graph_exec.clear();
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  h->cap_stream = nullptr;
   void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
                   h->Fre, h->Fim, h->Jre, h->Jim, h->Bre, h->Bim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
                   h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
@@ -903,6 +957,12 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
     rc = h->prec == CMCG_FP32 ? autotune<float>(h, STAGE_FORMS_F32, opt.stage_overlap)
                               : autotune<double>(h, STAGE_FORMS_F64, opt.stage_overlap);
     if (rc) return fail(rc);
+  }
+  h->graphs = opt.launch_graphs != 2;
+  if (h->graphs && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    h->cap_stream = nullptr;
+    h->graphs = false;
   }
   h->launches = 0;
   *out = h;

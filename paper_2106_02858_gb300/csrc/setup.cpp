@@ -60,6 +60,7 @@ int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* 
   if (opt->steps_per_period < 0) return fail(why, "steps_per_period < 0", CMCG_ERR_INVALID_ARG);
   if (opt->stage_variant < 0) return fail(why, "stage_variant < 0", CMCG_ERR_INVALID_ARG);
   if (opt->stage_overlap < 0 || opt->stage_overlap > 2) return fail(why, "stage_overlap not in 0..2", CMCG_ERR_INVALID_ARG);
+  if (opt->launch_graphs < 0 || opt->launch_graphs > 2) return fail(why, "launch_graphs not in 0..2", CMCG_ERR_INVALID_ARG);
   const int64_t nt = mesh->nt, nv = mesh->nv;
   const double* Xv = mesh->verts;
   const int32_t* T = mesh->tets;

@@ -300,3 +300,25 @@ def test_fw_batch_approaches_cmcg_and_matches_single(lib):
     eb, hb = lib.cmcg_fw_solve_batch(h, [p.j_re], [p.j_im], 12)
     assert np.array_equal(eb[0], e) and np.array_equal(hb[0], hh)
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_and_direct_launches_agree(lib, prec):
+    """Sweeps replayed from CUDA graphs (the default) and launched directly give the same
+    bits: forward and adjoint periods, a filtered source period and a whole CMCG solve."""
+    p = _problem("cube3", 2)
+    P = lib.CMCG_FP64 if prec == "fp64" else lib.CMCG_FP32
+    U = I.random_field(np.random.default_rng(21), p.nt, 2)
+    outs = []
+    for graphs in (0, 2):
+        h, _ = lib.create_for_problem(p, precision=P, stage_variant=1, launch_graphs=graphs)
+        r = [lib.dgtd_period_forward(h, U), lib.dgtd_period_adjoint(h, U)]
+        r += list(lib.dgtd_period_forward(h, U, p.j_re, p.j_im, filtered=True))
+        e, hh, info = lib.cmcg_solve(h, p.j_re, p.j_im, 1e-6, 200)
+        r += [e, hh]
+        r.append(lib.dgtd_period_forward(h, U))  # a replay of the first graph
+        outs.append(r)
+        h.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+    assert np.array_equal(outs[0][0], outs[0][-1])
