@@ -205,6 +205,107 @@ def replica_throughput(local_s: float, steps: int, world: int, device=None):
 
 
 # ---------------------------------------------------------------------------------------------
+# Secondary workloads: batched right-hand sides and a served request stream.
+# ---------------------------------------------------------------------------------------------
+
+def measure_batched_rhs(cmcg, I, reps: int = 3):
+    """32 Gaussian sources on the 384-tet cube at P3 (omega = 4 pi) in one batch handle, FP32
+    sweeps, CG to 1e-6 per source; timed through the host-buffer batch entry."""
+    prob = I.batched_rhs(nrhs=32)
+    mesh = cmcg.make_mesh(prob.mesh.verts, prob.mesh.tets, prob.mesh.tags)
+    nrhs = prob.j_re.shape[0]
+    opt = cmcg.cmcg_default_options(order=prob.order, precision=cmcg.CMCG_FP32)
+    h = cmcg.cmcg_create_batch([(mesh, prob.eps, prob.mu, prob.omega)] * nrhs, opt)
+    jr, ji = list(prob.j_re), list(prob.j_im)
+    cmcg.cmcg_solve_batch(h, jr, ji, prob.tol, MAX_ITER)  # warm-up (captures the sweep graphs)
+    cmcg.cmcg_profile_enable(h, True)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _e, _h, infos = cmcg.cmcg_solve_batch(h, jr, ji, prob.tol, MAX_ITER)
+    dt = (time.perf_counter() - t0) / reps
+    free_ms, free_stages, _sm, _ss = cmcg.cmcg_profile_read(h)
+    steps = cmcg.cmcg_get_problem(h, 0)[1]
+    periods = sum(3 + 2 * i.iters for i in infos)
+    h.close()
+    return {"workload": "384-tet cube, P3, omega = 4 pi, 32 Gaussian sources in one handle, FP32, CG 1e-6",
+            "solves_per_s": nrhs / dt, "ms_per_batch": dt * 1e3,
+            "dof_updates_per_s": prob.nt * 6 * prob.np_ * steps * periods / dt,
+            "cg_iters": [i.iters for i in infos][:4] + ["..."],
+            "us_per_stage_launch": 1e3 * free_ms / max(free_stages, 1),
+            "note": "working set L2-resident: HBM fraction not meaningful"}
+
+
+def measure_serving(cmcg, I, rate_hz: float = 150.0, n_small: int = 150, n_large: int = 3, seed: int = 0,
+                    workers: int = 8, max_batch: int = 16, max_wait_ms: float = 5.0):
+    """A Poisson stream through the serving runtime (continuous batching: `workers` threads with
+    their own streams, batches of up to `max_batch`): small requests are one P3 source on the
+    384-tet cube (the batched-RHS shape), large ones a 12^3-cube P2 problem; latency = submit to
+    result, as the server reports it."""
+    import threading
+    import numpy as np
+    small = I.batched_rhs(nrhs=32)
+    large = I.cube_problem(12, 2, 4 * math.pi, (0.4, 0.5, 0.6), (0.0, 1.0, 0.0), 0.1, tol=1e-6)
+    opt = cmcg.cmcg_server_default_options(precision=cmcg.CMCG_FP32, max_batch=max_batch, workers=workers,
+                                           max_wait_ms=max_wait_ms, tol=1e-6, max_iter=MAX_ITER)
+    srv = cmcg.cmcg_server_create(opt)
+    ms = cmcg.make_mesh(small.mesh.verts, small.mesh.tets, small.mesh.tags)
+    ml = cmcg.make_mesh(large.mesh.verts, large.mesh.tets, large.mesh.tags)
+    m_small = cmcg.cmcg_server_add_model(srv, ms, small.eps, small.mu, small.omega, small.order)
+    m_large = cmcg.cmcg_server_add_model(srv, ml, large.eps, large.mu, large.omega, large.order, max_batch=2)
+    # warm-up: one batch of each model (graphs captured, handles pooled)
+    for t in [cmcg.cmcg_server_submit(srv, m_small, small.j_re[k]) for k in range(8)]:
+        cmcg.cmcg_server_poll(srv, t, m_small, wait=True)
+    cmcg.cmcg_server_poll(srv, cmcg.cmcg_server_submit(srv, m_large, large.j_re), m_large, wait=True)
+    rng = np.random.default_rng(seed)
+    n = n_small + n_large
+    kinds = np.array([0] * n_small + [1] * n_large)
+    rng.shuffle(kinds)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate_hz, n))
+    tickets = [None] * n
+
+    def submitter():
+        t0 = time.perf_counter()
+        for k in range(n):
+            wait = arrivals[k] - (time.perf_counter() - t0)
+            if wait > 0:
+                time.sleep(wait)
+            if kinds[k] == 0:
+                tickets[k] = cmcg.cmcg_server_submit(srv, m_small, small.j_re[k % 32])
+            else:
+                tickets[k] = cmcg.cmcg_server_submit(srv, m_large, large.j_re)
+
+    t_start = time.perf_counter()
+    th = threading.Thread(target=submitter)
+    th.start()
+    th.join()
+    lat = {0: [], 1: []}
+    for k in range(n):
+        r = cmcg.cmcg_server_poll(srv, tickets[k], m_small if kinds[k] == 0 else m_large, wait=True)
+        lat[int(kinds[k])].append(r[4])
+    wall = time.perf_counter() - t_start
+    stats = cmcg.cmcg_server_stats(srv)
+    srv.close()
+    # the same small request as a serial FP64 plain solve, for comparison
+    h64, _m = cmcg.create_for_problem(small, precision=cmcg.CMCG_FP64)
+    cmcg.cmcg_solve(h64, small.j_re[0], None, 1e-6, MAX_ITER)
+    t0 = time.perf_counter()
+    cmcg.cmcg_solve(h64, small.j_re[1], None, 1e-6, MAX_ITER)
+    fp64_s = time.perf_counter() - t0
+    h64.close()
+    alls = lat[0] + lat[1]
+    pct = lambda xs, q: float(np.percentile(xs, q)) if xs else None
+    return {"workload": f"Poisson {rate_hz:g}/s: {n_small} small (384-tet cube P3, one source) + {n_large} "
+                        f"large (10,368-tet cube P2) requests, FP32, CG 1e-6, {workers} workers, "
+                        f"batches <= {max_batch}, window {max_wait_ms:g} ms",
+            "offered_per_s": rate_hz,
+            "solves_per_s": n / wall, "p50_ms": pct(alls, 50), "p99_ms": pct(alls, 99),
+            "small_p50_ms": pct(lat[0], 50), "small_p99_ms": pct(lat[0], 99),
+            "large_p50_ms": pct(lat[1], 50), "serial_fp64_plain_small_solves_per_s": 1.0 / fp64_s,
+            "handles": stats["handles"],
+            "device_bytes": stats["bytes_in_use"]}
+
+
+# ---------------------------------------------------------------------------------------------
 # Arms.
 # ---------------------------------------------------------------------------------------------
 
@@ -354,6 +455,12 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                         / FP32_PEAK_TFLOPS, "peak_source": "unit counts x maximum SM clock"},
                 "algorithmic_bytes_per_launch": alg, "avg_launch_us": stage_us, "peak_source": peak_kind}
 
+    batched = serving = None
+    if rank == 0 and not args.skip_extra:
+        batched = measure_batched_rhs(cmcg, I)
+        serving = [measure_serving(cmcg, I, rate_hz=40.0, n_small=160, n_large=2),
+                   measure_serving(cmcg, I, rate_hz=160.0, n_small=320, n_large=4, seed=1)]
+
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
         r = oracle_sample(2, 0)
@@ -386,6 +493,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "roofline": roofline,
             "clocks": clocks,
             "fw_at_equal_periods": fw,
+            "batched_rhs": batched,
+            "serving": serving,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -422,6 +531,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fw", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true", help="skip the batched-RHS and serving measurements")
     ap.add_argument("--profile-sweep", action="store_true", help="run one period sweep only (for ncu)")
     ap.add_argument("--stage-variant", type=int, default=0, help="force a stage-kernel form (see cmcg_options)")
     args = ap.parse_args()
