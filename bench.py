@@ -453,7 +453,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
                         "frac": stage_algorithmic_flops(prob.nt, prob.order) / (stage_us * 1e-6) / 1e12
                         / FP32_PEAK_TFLOPS, "peak_source": "unit counts x maximum SM clock"},
-                "algorithmic_bytes_per_launch": alg, "avg_launch_us": stage_us, "peak_source": peak_kind}
+                "algorithmic_bytes_per_launch": alg, "avg_launch_us": stage_us, "peak_source": peak_kind,
+                "source_stage_us": src_ms * 1e3 / max(src_stages, 1)}
 
     batched = serving = None
     if rank == 0 and not args.skip_extra:

@@ -171,6 +171,16 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
       }
     }
   }
+  // Source stages (classic RK form): the accumulator rows this thread updates at the end,
+  // fetched now so that their latency overlaps the volume and face work.
+  R* acc_s = tr + TRACE_SLOTS * STAGE_THREADS;
+  if (a.acc_out) {
+#pragma unroll
+    for (int k = 0; k < 3 * NP; ++k) {
+      if constexpr (sizeof(R) == 4) cp_async_4(acc_s + k * STAGE_THREADS, a.acc_in + off + k * TILE);
+      else cp_async_8(acc_s + k * STAGE_THREADS, a.acc_in + off + k * TILE);
+    }
+  }
   cp_async_commit();
 
   R phi[3][NP];
@@ -283,7 +293,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
 #pragma unroll
       for (int n = 0; n < NP; ++n) {
         const int64_t o = off + (c * NP + n) * TILE;
-        a.acc_out[o] = a.acc_in[o] + cf.c_acc * phi[c][n];
+        a.acc_out[o] = acc_s[(c * NP + n) * STAGE_THREADS] + cf.c_acc * phi[c][n];
       }
   }
   if (a.out) {
@@ -562,9 +572,11 @@ __global__ void __launch_bounds__(QD_THREADS, MINB) dg_stage_quad(const StageArg
 
 }  // namespace
 
+// Dynamic shared memory of the two-thread kernel: the trace slots, plus the accumulator
+// rows in source stages (acc = true).
 template <typename R>
-constexpr size_t stage_smem() {
-  return size_t(TRACE_SLOTS) * STAGE_THREADS * sizeof(R);
+constexpr size_t stage_smem(bool acc = false) {
+  return size_t(TRACE_SLOTS + (acc ? 3 * NPQ : 0)) * STAGE_THREADS * sizeof(R);
 }
 
 template <typename Arg>
@@ -587,7 +599,8 @@ template <>
 void launch_stage<CMCG_Q, float>(const StageArgs<float>& a, cudaStream_t s, int form, bool pdl) {
   const unsigned blocks = unsigned((2 * a.nti + STAGE_THREADS - 1) / STAGE_THREADS);
   const unsigned qblocks = unsigned(a.nti / TILE);  // one block per tile
-  constexpr size_t sm = stage_smem<float>(), qsm = quad_smem<float>();
+  const size_t sm = stage_smem<float>(a.acc_out != nullptr);
+  constexpr size_t qsm = quad_smem<float>();
   switch (form) {
     case 1: launch_k(dg_stage_kernel<float, 3>, blocks, STAGE_THREADS, sm, s, pdl, a); break;
     case 2: launch_k(dg_stage_kernel<float, 4>, blocks, STAGE_THREADS, sm, s, pdl, a); break;
@@ -605,17 +618,17 @@ void launch_stage<CMCG_Q, double>(const StageArgs<double>& a, cudaStream_t s, in
   switch (form) {
     case 1: launch_k(dg_stage_quad<double, 2>, qblocks, QD_THREADS, qsm, s, pdl, a); break;
     case 2: launch_k(dg_stage_quad<double, 3>, qblocks, QD_THREADS, qsm, s, pdl, a); break;
-    default: launch_k(dg_stage_kernel<double, 1>, blocks, STAGE_THREADS, stage_smem<double>(), s, pdl, a); break;
+    default: launch_k(dg_stage_kernel<double, 1>, blocks, STAGE_THREADS, stage_smem<double>(a.acc_out != nullptr), s, pdl, a); break;
   }
 }
 
 template <>
 void upload_constants<CMCG_Q>(const RefMats& rm) {
   // allow the dynamic shared memory of the trace prefetch beyond the 48 KiB default
-  cudaFuncSetAttribute(dg_stage_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(stage_smem<float>()));
-  cudaFuncSetAttribute(dg_stage_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(stage_smem<float>()));
-  cudaFuncSetAttribute(dg_stage_kernel<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(stage_smem<float>()));
-  cudaFuncSetAttribute(dg_stage_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(stage_smem<double>()));
+  cudaFuncSetAttribute(dg_stage_kernel<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(stage_smem<float>(true)));
+  cudaFuncSetAttribute(dg_stage_kernel<float, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(stage_smem<float>(true)));
+  cudaFuncSetAttribute(dg_stage_kernel<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(stage_smem<float>(true)));
+  cudaFuncSetAttribute(dg_stage_kernel<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(stage_smem<double>(true)));
   cudaFuncSetAttribute(dg_stage_quad<float, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<float>()));
   cudaFuncSetAttribute(dg_stage_quad<float, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<float>()));
   cudaFuncSetAttribute(dg_stage_quad<float, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<float>()));
