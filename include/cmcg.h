@@ -369,7 +369,8 @@ int cmcg_profile_read(cmcg_handle* h, double* free_ms, int64_t* free_stages, dou
  * server's device memory stays within hbm_budget_bytes (0 = no limit);
  * otherwise a batch waits for a pooled handle.  Every handle of a model uses
  * the kernel form chosen when the model was registered, so a request's result
- * is the one it gets when solved alone, whatever shares its batch. */
+ * is the one it gets when solved alone, whatever shares its batch.  Requests
+ * carry a volume source only (no impedance-face data). */
 typedef struct cmcg_server cmcg_server;
 
 typedef struct cmcg_server_options {

@@ -1316,11 +1316,18 @@ int cmcg_set_boundary_data(cmcg_handle* h, int problem, const double* g_re, cons
     }
     // The data term of Phi is linear in g: with the exterior state (g, 0) the flux of a face gains
     // aE (g - n (n.g)) on the E rows and bH n x g on the H rows, lifted like every flux.  Summed
-    // here once per call in double precision, in the field layout of the problem's tiles.
+    // here once per call in double precision for the tetrahedra with impedance faces only, then
+    // scattered into the problem's zeroed rows.
     const RefMats& rm = ref_mats(h->q);
-    std::vector<double> hre(cnt, 0.0), him(cnt, 0.0);
+    const int rows = 6 * np;
+    std::map<int64_t, int64_t> slot;  // internal tetrahedron -> compact row block
+    for (const ImpFace& F : P.imp) slot.emplace(F.it, int64_t(slot.size()));
+    std::vector<int64_t> tets(slot.size());
+    for (const auto& kv : slot) tets[kv.second] = kv.first;
+    std::vector<double> hre(tets.size() * rows, 0.0), him(tets.size() * rows, 0.0);
     for (const ImpFace& F : P.imp) {
-      const int64_t li = F.it - P.tet0, tile = li / TILE, lane = li % TILE;
+      double* re = hre.data() + slot[F.it] * rows;
+      double* im = him.data() + slot[F.it] * rows;
       for (int jf = 0; jf < nfp; ++jf) {
         double fE[2][3], fH[2][3];
         for (int part = 0; part < 2; ++part) {
@@ -1339,27 +1346,46 @@ int cmcg_set_boundary_data(cmcg_handle* h, int problem, const double* g_re, cons
         for (int i = 0; i < np; ++i) {
           const double L = rm.LIFT[size_t(i) * 4 * nfp + F.f * nfp + jf];
           for (int c = 0; c < 3; ++c) {
-            const size_t oE = size_t(tile) * 6 * np * TILE + size_t(c * np + i) * TILE + lane;
-            const size_t oH = size_t(tile) * 6 * np * TILE + size_t((3 + c) * np + i) * TILE + lane;
-            hre[oE] += L * fE[0][c];
-            him[oE] += L * fE[1][c];
-            hre[oH] += L * fH[0][c];
-            him[oH] += L * fH[1][c];
+            re[c * np + i] += L * fE[0][c];
+            im[c * np + i] += L * fE[1][c];
+            re[(3 + c) * np + i] += L * fH[0][c];
+            im[(3 + c) * np + i] += L * fH[1][c];
           }
         }
       }
     }
-    // copies ordered after the zeroing above on the handle's stream; host buffers live until the sync
-    if (h->prec == CMCG_FP32) {
-      std::vector<float> fre(hre.begin(), hre.end()), fim(him.begin(), him.end());
-      CK(cudaMemcpyAsync(static_cast<float*>(h->Bre) + off, fre.data(), cnt * 4, cudaMemcpyHostToDevice, h->stream));
-      CK(cudaMemcpyAsync(static_cast<float*>(h->Bim) + off, fim.data(), cnt * 4, cudaMemcpyHostToDevice, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemsetAsync(static_cast<char*>(h->Bre) + off * R_, 0, cnt * R_, h->stream));
+    CK(cudaMemsetAsync(static_cast<char*>(h->Bim) + off * R_, 0, cnt * R_, h->stream));
+    if (!tets.empty()) {
+      double *dre = nullptr, *dim = nullptr;
+      int64_t* dtet = nullptr;
+      const size_t vb = hre.size() * sizeof(double);
+      if (cudaMalloc(&dre, vb) != cudaSuccess || cudaMalloc(&dim, vb) != cudaSuccess ||
+          cudaMalloc(&dtet, tets.size() * sizeof(int64_t)) != cudaSuccess) {
+        cudaFree(dre);
+        cudaFree(dim);
+        cudaFree(dtet);
+        return CMCG_ERR_OUT_OF_MEMORY;
+      }
+      cudaError_t e = cudaMemcpyAsync(dre, hre.data(), vb, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(dim, him.data(), vb, cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dtet, tets.data(), tets.size() * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream);
+      if (e == cudaSuccess) {
+        if (h->prec == CMCG_FP32)
+          launch_scatter_rows<float>((float*)h->Bre, (float*)h->Bim, dre, dim, dtet, int64_t(tets.size()), np,
+                                     h->stream);
+        else
+          launch_scatter_rows<double>((double*)h->Bre, (double*)h->Bim, dre, dim, dtet, int64_t(tets.size()), np,
+                                      h->stream);
+        e = cudaGetLastError();
+      }
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // host buffers live until here
+      cudaFree(dre);
+      cudaFree(dim);
+      cudaFree(dtet);
+      if (e != cudaSuccess) return cuda_fail(e);
     } else {
-      CK(cudaMemcpyAsync(static_cast<double*>(h->Bre) + off, hre.data(), cnt * 8, cudaMemcpyHostToDevice,
-                         h->stream));
-      CK(cudaMemcpyAsync(static_cast<double*>(h->Bim) + off, him.data(), cnt * 8, cudaMemcpyHostToDevice,
-                         h->stream));
       CK(cudaStreamSynchronize(h->stream));
     }
     P.has_bdata = true;

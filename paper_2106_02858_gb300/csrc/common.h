@@ -184,6 +184,11 @@ void launch_cg_update(int q, R* U0, R* Rv, const R* D, const R* A, const double*
 template <typename R>
 void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* partials, const BlockTable& bt,
                 cudaStream_t s);
+// Writes `count` tetrahedra's 6 Np rows (src: [count][6 Np], double) into two field vectors
+// (re, im) at internal tetrahedra tet[i]; other tetrahedra are untouched.
+template <typename R>
+void launch_scatter_rows(R* dst_re, R* dst_im, const double* src_re, const double* src_im, const int64_t* tet,
+                         int64_t count, int np, cudaStream_t s);
 // D = R + beta_p D and Uw = D on the tiles of active problems.
 template <typename R>
 void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob, const int32_t* pactive,

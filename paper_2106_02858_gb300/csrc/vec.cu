@@ -218,6 +218,18 @@ __global__ void __launch_bounds__(DOT_THREADS) dot_kernel(const R* X, const R* Y
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+template <typename R>
+__global__ void scatter_rows_kernel(R* dst_re, R* dst_im, const double* src_re, const double* src_im,
+                                    const int64_t* tet, int64_t count, int rows) {
+  const int64_t n = count * rows;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / rows, k = i % rows, t = tet[e];
+    const int64_t o = (t >> 5) * rows * TILE + k * TILE + (t & 31);
+    dst_re[o] = R(src_re[i]);
+    dst_im[o] = R(src_im[i]);
+  }
+}
+
 // D = R + beta_p D; Uw = D (active problems only).
 template <typename R>
 __global__ void cg_direction_kernel(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob,
@@ -357,6 +369,13 @@ void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* parti
   CMCG_DISPATCH_Q(q, dot_kernel, X, Y, wdot, partials, bt);
 }
 template <typename R>
+void launch_scatter_rows(R* dst_re, R* dst_im, const double* src_re, const double* src_im, const int64_t* tet,
+                         int64_t count, int np, cudaStream_t s) {
+  if (count <= 0) return;
+  scatter_rows_kernel<R><<<grid_for(count * 6 * np, 256), 256, 0, s>>>(dst_re, dst_im, src_re, src_im, tet, count,
+                                                                         6 * np);
+}
+template <typename R>
 void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob, const int32_t* pactive,
                          int64_t n, int np, cudaStream_t s) {
   cg_direction_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(D, Uw, Rv, sc, tprob, pactive, n, int64_t(6) * np * TILE);
@@ -377,6 +396,8 @@ void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, 
   template void launch_cg_update<R>(int, R*, R*, const R*, const R*, const double*, const Scalars*, double*,          \
                                     const BlockTable&, const int32_t*, cudaStream_t);                                 \
   template void launch_dot<R>(int, const R*, const R*, const double*, double*, const BlockTable&, cudaStream_t);      \
+  template void launch_scatter_rows<R>(R*, R*, const double*, const double*, const int64_t*, int64_t, int,        \
+                                       cudaStream_t);                                                              \
   template void launch_cg_direction<R>(R*, R*, const R*, const Scalars*, const int32_t*, const int32_t*, int64_t,     \
                                        int, cudaStream_t);
 CMCG_INST(float)
