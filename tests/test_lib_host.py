@@ -6,7 +6,9 @@
 * ``cmcg_reference_matrices`` (monomial basis, exact simplex integrals, Duffy
   quadrature on the unit tetrahedron) equals the oracle's Dubiner-based
   matrices after the change of reference tetrahedron.
-* Without a GPU, ``cmcg_create`` fails cleanly with CMCG_ERR_NO_DEVICE.
+* Without a GPU, ``cmcg_create`` and ``cmcg_server_create`` fail cleanly with
+  CMCG_ERR_NO_DEVICE; every entry rejects a NULL handle or server, bad options
+  and empty inputs with CMCG_ERR_INVALID_ARG before touching the device.
 * The product package never imports the oracle.
 """
 import ast
@@ -144,3 +146,74 @@ def test_product_package_never_imports_the_oracle():
             src = open(os.path.join(ROOT, "oracle", f)).read()
             for mod in re.findall(r"from (paper_2106_02858_gb300[\w.]*) import", src):
                 assert mod == "paper_2106_02858_gb300.inputs", (f, mod)
+
+
+def test_every_handle_entry_rejects_a_null_handle(lib):
+    """Each entry that takes a handle or a server returns CMCG_ERR_INVALID_ARG for NULL, without
+    touching the device (the argument checks come before any CUDA call)."""
+    L = lib._lib
+    INV = lib.CMCG_ERR_INVALID_ARG
+    d = np.zeros(8)
+    p = d.ctypes.data_as(lib._dp)
+    pp = (lib._dp * 1)(p)
+    import ctypes as C
+    info = lib.cmcg_info()
+    calls = {
+        "cmcg_set_stream": lambda: L.cmcg_set_stream(None, None),
+        "cmcg_get_sizes": lambda: L.cmcg_get_sizes(None, None, None, None, None, None),
+        "cmcg_get_tuning": lambda: L.cmcg_get_tuning(None, None, None),
+        "cmcg_get_problem": lambda: L.cmcg_get_problem(None, 0, None, None, None),
+        "dgtd_apply": lambda: L.dgtd_apply(None, 0.0, p, None, None, 0, p),
+        "dgtd_period_forward": lambda: L.dgtd_period_forward(None, p, None, None, p, None, None),
+        "dgtd_period_adjoint": lambda: L.dgtd_period_adjoint(None, p, p),
+        "cmcg_solve": lambda: L.cmcg_solve(None, p, None, 1e-6, 10, p, p, p, p, C.byref(info)),
+        "cmcg_solve_batch": lambda: L.cmcg_solve_batch(None, pp, None, 1e-6, 10, pp, pp, pp, pp, None),
+        "cmcg_solve_batch_n": lambda: L.cmcg_solve_batch_n(None, 1, pp, None, 1e-6, 10, pp, pp, pp, pp, None),
+        "cmcg_fw_solve": lambda: L.cmcg_fw_solve(None, p, None, 2, p, p, p, p),
+        "cmcg_fw_solve_batch": lambda: L.cmcg_fw_solve_batch(None, 2, pp, None, pp, pp, pp, pp),
+        "cmcg_set_boundary_data": lambda: L.cmcg_set_boundary_data(None, 0, p, None),
+        "cmcg_inner": lambda: L.cmcg_inner(None, p, p, None),
+        "cmcg_profile_enable": lambda: L.cmcg_profile_enable(None, 1),
+        "cmcg_profile_read": lambda: L.cmcg_profile_read(None, None, None, None, None),
+        "cmcg_server_add_model": lambda: L.cmcg_server_add_model(None, None, p, p, 1.0, 1, 0, None),
+        "cmcg_server_submit": lambda: L.cmcg_server_submit(None, 0, p, None, None),
+        "cmcg_server_poll": lambda: L.cmcg_server_poll(None, 1, 0, p, p, p, p, None, None),
+        "cmcg_server_stats": lambda: L.cmcg_server_stats(None, None, None, None, None),
+    }
+    for name, call in calls.items():
+        assert call() == INV, name
+    assert L.cmcg_batch_size(None) <= 0
+    assert L.cmcg_kernel_launches(None) == 0
+    assert L.cmcg_device_bytes(None) == 0
+    L.cmcg_destroy(None)
+    L.cmcg_server_destroy(None)
+
+
+def test_server_options_are_checked_before_the_device(lib):
+    import torch
+    for bad in (dict(max_batch=0), dict(workers=0), dict(workers=65), dict(max_wait_ms=-1.0), dict(tol=-1.0),
+                dict(max_iter=-1)):
+        with pytest.raises(lib.CMCGError) as ei:
+            lib.cmcg_server_create(lib.cmcg_server_default_options(**bad))
+        assert ei.value.code == lib.CMCG_ERR_INVALID_ARG, bad
+    if not torch.cuda.is_available():
+        with pytest.raises(lib.CMCGError) as ei:
+            lib.cmcg_server_create(lib.cmcg_server_default_options())
+        assert ei.value.code in (lib.CMCG_ERR_NO_DEVICE, lib.CMCG_ERR_CUDA)
+
+
+def test_empty_and_undersized_inputs_are_rejected(lib):
+    m = _mesh(1)
+    eps, mu = np.ones(m.nt), np.ones(m.nt)
+    opt = lib.cmcg_default_options(order=1)
+    empty = lib.make_mesh(m.verts, m.tets[:0], m.tags[:0])
+    assert lib.cmcg_validate(empty, eps[:0], mu[:0], 2 * np.pi, opt)[0] == lib.CMCG_ERR_INVALID_ARG
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, 0.0, opt)[0] == lib.CMCG_ERR_INVALID_ARG
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, np.zeros(m.nt), 2 * np.pi, opt)[0] == \
+        lib.CMCG_ERR_INVALID_ARG
+    bad_opt = lib.cmcg_default_options(order=1, steps_per_period=-1)
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, 2 * np.pi, bad_opt)[0] == \
+        lib.CMCG_ERR_INVALID_ARG
+    bad_opt = lib.cmcg_default_options(order=1, launch_graphs=3)
+    assert lib.cmcg_validate(lib.make_mesh(m.verts, m.tets, m.tags), eps, mu, 2 * np.pi, bad_opt)[0] == \
+        lib.CMCG_ERR_INVALID_ARG
