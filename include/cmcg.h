@@ -50,6 +50,21 @@
  * CMCG_ERR_NONFINITE when a reduction is not finite.
  *
  * Threading: one handle per host thread at a time.
+ *
+ * Typical use (error checks omitted):
+ *
+ *   cmcg_options o;  cmcg_default_options(&o);
+ *   o.order = 2;  o.precision = CMCG_FP32;            // FP32 sweeps, FP64 CG scalars
+ *   cmcg_mesh m = {nv, verts, nt, tets, face_tags};
+ *   cmcg_handle* h;  cmcg_create(&m, eps, mu, omega, &o, &h);   // validates, lays out, tunes
+ *   cmcg_info info;
+ *   cmcg_solve(h, j_re, j_im, 1e-6, 1000, e_re, e_im, h_re, h_im, &info);
+ *   cmcg_destroy(h);
+ *
+ * Many sources or meshes of one order: cmcg_create_batch + cmcg_solve_batch.
+ * Incident fields on impedance faces: cmcg_set_boundary_data before the solve.
+ * The limiting-amplitude baseline: cmcg_fw_solve.  A request server with
+ * continuous batching: cmcg_server_create / add_model / submit / poll.
  */
 #ifndef CMCG_H
 #define CMCG_H
