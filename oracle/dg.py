@@ -6,8 +6,10 @@ oracle applies the 3D generalisation with the PDE's own sign convention
 eps dE/dt + curl H = J, mu dH/dt - curl E = 0 (Eq. maxwell_time_strong), in
 strong form on each tetrahedron K with outward normal n:
 
-  dE/dt = eps^{-1} [ J - curl H - M^{-1} oint n x (H^ - H^-) ]
+  dE/dt = eps^{-1} [ J - sigma E - curl H - M^{-1} oint n x (H^ - H^-) ]
   dH/dt = mu^{-1}  [ curl E + M^{-1} oint n x (E^ - E^-) ]
+
+(sigma: the conductivity of Section 2.1, per tetrahedron; 0 unless the geometry carries one)
 
 with the upwind (Riemann) numerical traces of Section 5.2.2, the paper's
 "avg" read as the mean:
@@ -141,6 +143,8 @@ def apply_B(U: np.ndarray, geo: Geometry, adjoint: bool = False, flux: str = "up
     liftH = np.einsum("nfj,...kfcj->...kcn", L, fH * scale)
     out = np.empty_like(U)
     out[..., :3, :] = (-curlH - liftE) / geo.eps[:, None, None]
+    if geo.sigma is not None:
+        out[..., :3, :] -= (geo.sigma / geo.eps)[:, None, None] * E
     out[..., 3:, :] = (curlE + liftH) / geo.mu[:, None, None]
     return out
 

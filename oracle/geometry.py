@@ -13,6 +13,7 @@ Test infrastructure only.
 from __future__ import annotations
 
 from dataclasses import dataclass
+from typing import Optional
 
 import numpy as np
 
@@ -38,13 +39,14 @@ class Geometry:
     eps: np.ndarray
     mu: np.ndarray
     nodes: np.ndarray  # (nt, Np, 3)
+    sigma: Optional[np.ndarray] = None  # (nt,) conductivity (Section 2.1); None = 0
 
 
 class MeshError(ValueError):
     pass
 
 
-def build_geometry(verts, tets, tags, eps, mu, q: int) -> Geometry:
+def build_geometry(verts, tets, tags, eps, mu, q: int, sigma=None) -> Geometry:
     R = ref_element(q)
     verts = np.asarray(verts, dtype=np.float64)
     tets = np.asarray(tets, dtype=np.int64)
@@ -107,4 +109,5 @@ def build_geometry(verts, tets, tags, eps, mu, q: int) -> Geometry:
 
     return Geometry(q=q, nt=nt, J=J, G=G, normals=normals, area=area, sJ=area / 2.0, volume=volume, rho=rho,
                     nbr=nbr_tet, nbr_face=nbr_face, mapP=mapP, bc=bc, eps=np.asarray(eps, np.float64),
-                    mu=np.asarray(mu, np.float64), nodes=nodes)
+                    mu=np.asarray(mu, np.float64), nodes=nodes,
+                    sigma=None if sigma is None else np.asarray(sigma, np.float64))
