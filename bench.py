@@ -45,7 +45,8 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dg_stage_scatterer24_P2_fp32.m
 STAGE_SRC = os.path.join(ROOT, "paper_2106_02858_gb300", "csrc", "dg_stage.cuh")
 # FP32 stage-kernel forms, indexed by cmcg_options.stage_variant - 1.
 STAGE_FORMS = ["dg_stage_kernel<float, 1>", "dg_stage_kernel<float, 3>", "dg_stage_kernel<float, 4>",
-               "dg_stage_quad<float, 4>", "dg_stage_quad<float, 5>", "dg_stage_quad<float, 6>"]
+               "dg_stage_quad<float, 4>", "dg_stage_quad<float, 5>", "dg_stage_quad<float, 6>",
+               "dg_stage_tc (tcgen05 3xTF32)"]
 
 
 def peaks():

@@ -47,7 +47,9 @@
  * |(I - P) D| > 100 |D| in the (eps, mu) norm (the period map grows the
  * energy by orders of magnitude: a step beyond the stability limit, e.g. a
  * forced steps_per_period), CMCG_ERR_CG_BREAKDOWN when (D, A) <= 0 and
- * CMCG_ERR_NONFINITE when a reduction is not finite.
+ * CMCG_ERR_NONFINITE when a reduction is not finite.  A stage kernel that
+ * waits on the tensor cores gives up after about one second and the call
+ * then returns CMCG_ERR_DEVICE_TIMEOUT (its outputs are not valid).
  *
  * Threading: one handle per host thread at a time.
  *
@@ -127,10 +129,13 @@ typedef struct cmcg_mesh {
  *                     FP32: 0, 1, 2 = two threads per tetrahedron (E / H)
  *                     with at least 1, 3, 4 resident 128-thread blocks per
  *                     SM; 3, 4, 5 = four threads per tetrahedron (E / H x
- *                     node half) with at least 4, 5, 6.  FP64: 0 = two
- *                     threads per tetrahedron; 1, 2 = four threads with at
- *                     least 2, 3.  Other k: CMCG_ERR_INVALID_ARG.  Results do
- *                     not depend on it beyond rounding.
+ *                     node half) with at least 4, 5, 6; 6 = the volume and
+ *                     lift contractions on the tensor cores (tcgen05, three
+ *                     TF32 products per FP32 product, FP32 accumulation),
+ *                     two threads per tetrahedron.  FP64: 0 = two threads
+ *                     per tetrahedron; 1, 2 = four threads with at least
+ *                     2, 3.  Other k: CMCG_ERR_INVALID_ARG.  Results do not
+ *                     depend on it beyond rounding.
  *   stage_overlap:    0 = decide by timing when the form is timed (on when
  *                     the form is forced); 1 = on; 2 = off.  On: each stage
  *                     is launched with programmatic stream serialisation, so
@@ -228,7 +233,7 @@ int cmcg_set_stream(cmcg_handle* h, void* stream);
 
 /* Stage-kernel form in use (0-based, as stage_variant - 1) and, when it was
  * chosen by timing at creation, the measured microseconds per stage of each
- * form (8 entries: [0..5] indexed by form, see stage_variant; [6] the chosen
+ * form (8 entries: [0..6] indexed by form, see stage_variant; [7] the chosen
  * form with stage_overlap on; -1 where not timed or rejected by the device).
  * Any pointer may be NULL. */
 int cmcg_get_tuning(const cmcg_handle* h, int* variant, double* us_per_stage);
@@ -417,7 +422,9 @@ int cmcg_server_submit(cmcg_server* s, int model, const double* j_re, const doub
  * running.  Otherwise (or once done) copies (e, h) (double[nt][3][Np] each; any
  * pointer may be NULL), the solve report, and latency_ms[0] = submit to
  * completion, latency_ms[1] = submit to start (may be NULL), forgets the
- * ticket and returns the request's status. */
+ * ticket and returns the request's status.  A ticket is taken by one poll:
+ * while one thread waits on it, a poll of the same ticket from another thread
+ * returns CMCG_ERR_INVALID_ARG (as does any poll after the result was taken). */
 int cmcg_server_poll(cmcg_server* s, int64_t ticket, int wait, double* e_re, double* e_im, double* h_re,
                      double* h_im, cmcg_info* info, double* latency_ms);
 

@@ -9,7 +9,9 @@ strong form on each tetrahedron K with outward normal n:
   dE/dt = eps^{-1} [ J - sigma E - curl H - M^{-1} oint n x (H^ - H^-) ]
   dH/dt = mu^{-1}  [ curl E + M^{-1} oint n x (E^ - E^-) ]
 
-(sigma: the conductivity of Section 2.1, per tetrahedron; 0 unless the geometry carries one)
+(sigma: the conductivity of Eq. maxwell_time_strong, Section 1, with the coefficients of
+Section 3.1; the discrete term (sigma E_h, v_h) of Section 5.2.2, per tetrahedron; 0 unless the
+geometry carries one)
 
 with the upwind (Riemann) numerical traces of Section 5.2.2, the paper's
 "avg" read as the mean:

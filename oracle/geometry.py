@@ -39,7 +39,7 @@ class Geometry:
     eps: np.ndarray
     mu: np.ndarray
     nodes: np.ndarray  # (nt, Np, 3)
-    sigma: Optional[np.ndarray] = None  # (nt,) conductivity (Section 2.1); None = 0
+    sigma: Optional[np.ndarray] = None  # (nt,) conductivity (Eq. maxwell_time_strong, Section 1; coefficients Section 3.1); None = 0
 
 
 class MeshError(ValueError):

@@ -108,7 +108,9 @@ struct cmcg_handle {
   std::map<std::tuple<int, const void*, bool>, cudaGraphExec_t> graph_exec;
   int form = 0;      // stage-kernel form (see launch_stage)
   bool pdl = false;  // stages launched with programmatic stream serialisation
-  double tune_us[8];
+  double tune_us[8];      // [0..6] per form, [7] the chosen form with overlapped launches
+  int32_t* err = nullptr;       // device status word of the stage kernels' bounded waits
+  int32_t* err_host = nullptr;  // pinned
   // sweep profiling
   bool prof = false;
   struct SweepEv {
@@ -278,6 +280,7 @@ void stage(cmcg_handle* h, StageArgs<R>& a, cudaStream_t st) {
   a.gface = (const R*)h->gface;
   a.nbr = h->nbr;
   a.nti = h->nti;
+  a.err = h->err;
   a.tprob = h->tprob;
   if (h->q == 1) launch_stage<1, R>(a, st, h->form, h->pdl);
   else if (h->q == 2) launch_stage<2, R>(a, st, h->form, h->pdl);
@@ -497,7 +500,7 @@ int autotune(cmcg_handle* h, int nforms, int overlap) {
     double us;
     int rc = time_one(&us);
     if (rc) return rc;
-    h->tune_us[6] = us;
+    h->tune_us[7] = us;
     h->pdl = us >= 0 && us < best;
   } else {
     h->pdl = overlap == 1;
@@ -548,6 +551,17 @@ int set_source(cmcg_handle* h, const double* const* j_re, const double* const* j
   return CMCG_OK;
 }
 
+// Device status after a synchronised sweep: CMCG_ERR_DEVICE_TIMEOUT if a stage kernel's bounded
+// wait ran out (the word is then cleared for the next call).
+int check_err(cmcg_handle* h) {
+  CK(cudaMemcpyAsync(h->err_host, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (*h->err_host == 0) return CMCG_OK;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CMCG_ERR_DEVICE_TIMEOUT;
+}
+
 // Device-pointer period sweeps of a one-problem handle.
 template <typename R>
 int forward_dev(cmcg_handle* h, const double* u0, const double* j_re, const double* j_im, double* uT, double* fre,
@@ -570,8 +584,7 @@ int forward_dev(cmcg_handle* h, const double* u0, const double* j_re, const doub
     to_ext<R>(h, 0, h->Fim, 6, 0, fim, 6, 6);
   }
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->stream));
-  return CMCG_OK;
+  return check_err(h);
 }
 
 template <typename R>
@@ -580,8 +593,7 @@ int adjoint_dev(cmcg_handle* h, const double* wT, double* w0) {
   sweep_free<R>(h, true, nullptr);
   to_ext<R>(h, 0, h->Uw, 6, 0, w0, 6, 6);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->stream));
-  return CMCG_OK;
+  return check_err(h);
 }
 
 template <typename R>
@@ -615,8 +627,7 @@ int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, con
   stage<R>(h, a);
   to_ext<R>(h, 0, h->vA, 6, 0, out, 6, 6);
   CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->stream));
-  return CMCG_OK;
+  return check_err(h);
 }
 
 template <typename R>
@@ -635,9 +646,14 @@ int inner_dev(cmcg_handle* h, const double* u, const double* v, double* out) {
 int read_state(cmcg_handle* h) {
   CK(cudaMemcpyAsync(h->sc_host, h->sc, sizeof(Scalars) * h->nprob, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaMemcpyAsync(h->pactive_host, h->pactive, sizeof(int32_t) * h->nprob, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->err_host, h->err, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  return CMCG_OK;
+  if (*h->err_host == 0) return CMCG_OK;
+  CK(cudaMemsetAsync(h->err, 0, sizeof(int32_t), h->stream));  // cleared for the next call
+  CK(cudaStreamSynchronize(h->stream));
+  return CMCG_ERR_DEVICE_TIMEOUT;
 }
+
 
 // CMCG for problems [0, nused) of the handle (the others are skipped by every
 // kernel); j, e, h: one device pointer per used problem.
@@ -706,6 +722,7 @@ int solve_dev(cmcg_handle* h, int nused, const double* const* j_re, const double
   CK(cudaEventRecord(ev1, h->stream));
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(h->stream));
+  if ((rc = check_err(h))) return rc;
   float ms = 0;
   cudaEventElapsedTime(&ms, ev0, ev1);
   cudaEventDestroy(ev0);
@@ -753,7 +770,7 @@ int fw_dev(cmcg_handle* h, int periods, const double* const* j_re, const double*
     to_ext<R>(h, p, h->Fim, 6, 3, h_im[p], 3, 3);
   }
   CK(cudaGetLastError());
-  return CMCG_OK;
+  return check_err(h);
 }
 
 void free_all(cmcg_handle* h) {
@@ -764,12 +781,13 @@ void free_all(cmcg_handle* h) {
   void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
                   h->Fre, h->Fim, h->Jre, h->Jim, h->Bre, h->Bim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
                   h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
-                  h->ext0, h->ext1, h->ext2, h->ext3, h->used};
+                  h->ext0, h->ext1, h->ext2, h->ext3, h->used, h->err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->sc_host) cudaFreeHost(h->sc_host);
   if (h->pactive_host) cudaFreeHost(h->pactive_host);
   if (h->used_host) cudaFreeHost(h->used_host);
+  if (h->err_host) cudaFreeHost(h->err_host);
   for (auto& e : h->prof_ev) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -937,15 +955,17 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
             alloc(&h->Rv, vb) && alloc(&h->D, vb) && alloc(&h->A, vb) && alloc(&h->WT, vb) &&
             alloc((void**)&h->partials, sizeof(double) * 2 * std::max<size_t>(1, bt_tet0.size())) &&
             alloc((void**)&h->sc, sizeof(Scalars) * nprob) && alloc((void**)&h->pactive, sizeof(int32_t) * nprob) &&
-            alloc((void**)&h->used, sizeof(int32_t) * nprob) &&
+            alloc((void**)&h->used, sizeof(int32_t) * nprob) && alloc((void**)&h->err, sizeof(int32_t)) &&
             alloc((void**)&h->ext0, extlen) && alloc((void**)&h->ext1, extlen) && alloc((void**)&h->ext2, extlen) &&
             alloc((void**)&h->ext3, extlen);
   if (!ok) return fail(CMCG_ERR_OUT_OF_MEMORY);
   if (cudaMallocHost((void**)&h->sc_host, sizeof(Scalars) * nprob) != cudaSuccess ||
       cudaMallocHost((void**)&h->pactive_host, sizeof(int32_t) * nprob) != cudaSuccess ||
-      cudaMallocHost((void**)&h->used_host, sizeof(int32_t) * nprob) != cudaSuccess)
+      cudaMallocHost((void**)&h->used_host, sizeof(int32_t) * nprob) != cudaSuccess ||
+      cudaMallocHost((void**)&h->err_host, sizeof(int32_t)) != cudaSuccess)
     return fail(CMCG_ERR_OUT_OF_MEMORY);
-  if (cudaMemset(h->ACC, 0, vb) != cudaSuccess) return fail(CMCG_ERR_CUDA);
+  if (cudaMemset(h->ACC, 0, vb) != cudaSuccess || cudaMemset(h->err, 0, sizeof(int32_t)) != cudaSuccess)
+    return fail(CMCG_ERR_CUDA);
   rc = h->prec == CMCG_FP32 ? build_tables<float>(h) : build_tables<double>(h);
   if (rc) return fail(rc);
   if (opt.stage_variant > 0) {

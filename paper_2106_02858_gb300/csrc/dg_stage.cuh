@@ -36,6 +36,8 @@
 // reads back only the slots it filled (slot-major layout, conflict-free).
 #pragma once
 
+#include <cstring>
+
 #include "common.h"
 
 #ifndef CMCG_Q
@@ -570,6 +572,8 @@ __global__ void __launch_bounds__(QD_THREADS, MINB) dg_stage_quad(const StageArg
   else quad_stage<R, 0>(a);
 }
 
+#include "dg_stage_tc.cuh"
+
 }  // namespace
 
 // Dynamic shared memory of the two-thread kernel: the trace slots, plus the accumulator
@@ -607,6 +611,10 @@ void launch_stage<CMCG_Q, float>(const StageArgs<float>& a, cudaStream_t s, int 
     case 3: launch_k(dg_stage_quad<float, 4>, qblocks, QD_THREADS, qsm, s, pdl, a); break;
     case 4: launch_k(dg_stage_quad<float, 5>, qblocks, QD_THREADS, qsm, s, pdl, a); break;
     case 5: launch_k(dg_stage_quad<float, 6>, qblocks, QD_THREADS, qsm, s, pdl, a); break;
+    case STAGE_FORM_TC:
+      launch_k(dg_stage_tc<TC_MINB>, unsigned((a.nti + TC_TETS - 1) / TC_TETS), TC_THREADS,
+               tc_smem(a.acc_out != nullptr), s, pdl, a);
+      break;
     default: launch_k(dg_stage_kernel<float, 1>, blocks, STAGE_THREADS, sm, s, pdl, a); break;
   }
 }
@@ -634,6 +642,8 @@ void upload_constants<CMCG_Q>(const RefMats& rm) {
   cudaFuncSetAttribute(dg_stage_quad<float, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<float>()));
   cudaFuncSetAttribute(dg_stage_quad<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<double>()));
   cudaFuncSetAttribute(dg_stage_quad<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<double>()));
+  cudaFuncSetAttribute(dg_stage_tc<TC_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc_smem(true)));
+  tc_upload_reference(rm);
   const int np = rm.np, nfp = rm.nfp;
   std::vector<double> D(3 * np * np);
   for (int i = 0; i < np * np; ++i) {

@@ -51,6 +51,7 @@ struct Request {
   std::vector<double> jre, jim, ere, eim, hre, him;
   bool has_im = false;
   bool done = false;
+  bool claimed = false;  // a poll is waiting on it or has taken its result
   int status = CMCG_OK;
   cmcg_info info{};
   Clock::time_point t_submit, t_start, t_end;
@@ -304,10 +305,15 @@ int cmcg_server_poll(cmcg_server* s, int64_t ticket, int wait, double* e_re, dou
   auto it = s->reqs.find(ticket);
   if (it == s->reqs.end()) return CMCG_ERR_INVALID_ARG;
   Request* r = it->second.get();
+  // One poll per ticket takes the result: a second poll of a ticket that another thread is
+  // already waiting on is refused here, before it could wait on a request the first poll frees.
+  if (r->claimed) return CMCG_ERR_INVALID_ARG;
   if (!r->done) {
     if (!wait) return CMCG_PENDING;
+    r->claimed = true;
     s->cv_done.wait(lk, [&] { return r->done; });
   }
+  r->claimed = true;
   const size_t len = r->ere.size();
   if (r->status >= 0) {
     if (e_re) std::memcpy(e_re, r->ere.data(), len * 8);

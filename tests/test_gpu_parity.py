@@ -215,7 +215,8 @@ def test_hbm_budget_is_enforced(lib):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_every_stage_kernel_form_matches_oracle(lib, q, prec):
     """Each forced stage-kernel form (two or four threads per tetrahedron, each at several
-    occupancies) gives the oracle's sweeps: the autotuner's choice cannot change results."""
+    occupancies, and the tensor-core form) gives the oracle's sweeps: the autotuner's choice
+    cannot change results."""
     from oracle.timestep import Stepper
     p = _problem("scatterer8", q) if q < 3 else _problem("cube3", q)
     g = _geo(p)
@@ -224,7 +225,7 @@ def test_every_stage_kernel_form_matches_oracle(lib, q, prec):
     U = I.random_field(rng, p.nt, q)
     refF, refA = st.P(U), st.P_star(U)
     tol = 1e-12 if prec == "fp64" else 1e-5
-    forms = [1, 2, 3, 4, 5, 6, 7] if prec == "fp32" else [1, 2, 3, 4]
+    forms = [1, 2, 3, 4, 5, 6, 7, 8] if prec == "fp32" else [1, 2, 3, 4]
     tried = 0
     for k in forms:
         try:
@@ -237,7 +238,7 @@ def test_every_stage_kernel_form_matches_oracle(lib, q, prec):
         assert _rel(lib.dgtd_period_forward(h, U), refF, g) < tol, k
         assert _rel(lib.dgtd_period_adjoint(h, U), refA, g) < tol, k
         h.close()
-    assert tried == (6 if prec == "fp32" else 3)
+    assert tried == (7 if prec == "fp32" else 3)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])

@@ -1,4 +1,4 @@
-"""Pins of the oracle's conductivity term (Section 2.1: eps dE/dt + sigma E + curl H = J), no GPU.
+"""Pins of the oracle's conductivity term (Eq. maxwell_time_strong, Section 1: eps dE/dt + sigma E + curl H = J; coefficients Section 3.1, discrete term Section 5.2.2), no GPU.
 
 * Energy: with the centred flux and PEC walls the only loss is Ohmic, so
   (U, B U)_{eps,mu} = -sum_K sigma_K |J_K| E_K^T M E_K exactly (random sigma and U).
