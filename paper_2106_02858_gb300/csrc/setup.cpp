@@ -166,7 +166,10 @@ int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* 
   }
 
   // --- steps per period (Eq. cfl) ---------------------------------------------------------------
-  const double c_q = opt->c_q > 0 ? opt->c_q : (q == 1 ? 0.24 : 0.12);
+  // Section 5.3 prints c_1 = 0.24 (RK2) and c_3 = 0.12 (RK4) from 2D experiments.  In 3D the
+  // printed c_1 is not stable (on Kuhn meshes of 8^3 cubes and more with permittivity jumps one
+  // RK2 period multiplies a mode by 10 and more), so P1 uses half of it; P2 / P3 use 0.12.
+  const double c_q = opt->c_q > 0 ? opt->c_q : 0.12;
   const double Tper = 2.0 * M_PI / omega;
   int steps = opt->steps_per_period;
   if (steps <= 0) {

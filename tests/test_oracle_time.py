@@ -42,12 +42,43 @@ def test_cfl_step_count_matches_printed_constants():
     h = 0.25
     expected = math.ceil(1.0 / (gold["c1"] * h / (1 + math.sqrt(2))))
     assert expected == 41
-    assert steps_per_period(g, 2 * math.pi) == 41
+    assert steps_per_period(g, 2 * math.pi, c_q=gold["c1"]) == 41
+    # the 3D default for P1 is half the printed constant (see the next test)
+    assert steps_per_period(g, 2 * math.pi) == math.ceil(1.0 / (0.5 * gold["c1"] * h / (1 + math.sqrt(2)))) == 81
     g3, _ = _geo(4, 3)
     assert steps_per_period(g3, 4 * math.pi) == math.ceil(0.5 / (gold["c3"] * h / (1 + math.sqrt(2))))
     p = I.scatterer_sphere()
     g2 = build_geometry(p.mesh.verts, p.mesh.tets, p.mesh.tags, p.eps, p.mu, 2)
     assert steps_per_period(g2, p.omega) == math.ceil(0.5 / (0.12 * (1 / 24) / (1 + math.sqrt(2)))) == 242
+
+
+def test_printed_rk2_constant_grows_on_an_8_cube_with_permittivity_blocks():
+    """The printed c_1 = 0.24 is a 2D constant (Section 5.3).  On the 8^3 Kuhn cube with eps on a
+    2x2x2 block partition (P1, RK2, omega = 4 pi) power iteration on the oracle's period map
+    finds a mode that one period multiplies by about 11 at c_1 = 0.24, while at half the
+    constant, the 3D default, the period map does not grow (its largest factor tends to 1, the
+    static modes).  Smaller meshes (n <= 4) are stable at both constants."""
+    gold = json.load(open(GOLDEN))
+    p = I.block_eps_problem(8, 1, 4 * math.pi, np.random.default_rng(8))
+    g = build_geometry(p.mesh.verts, p.mesh.tets, p.mesh.tags, p.eps, p.mu, 1)
+    from oracle.dg import norm
+
+    def growth(c):
+        st = Stepper(g, p.omega, c_q=c)
+        u = I.random_field(np.random.default_rng(0), p.nt, 1)
+        u /= norm(u, g)
+        out = []
+        for _ in range(4):
+            v = st.P(u)
+            out.append(norm(v, g))
+            u = v / out[-1]
+        return st.M, out
+
+    M_printed, g_printed = growth(gold["c1"])
+    M_half, g_half = growth(0.5 * gold["c1"])
+    assert M_printed == 29 and M_half == 58
+    assert g_printed[-1] > 5.0
+    assert max(g_half) < 1.0 + 1e-9
 
 
 @pytest.mark.parametrize("q", [1, 2])
