@@ -46,7 +46,7 @@ STAGE_SRC = os.path.join(ROOT, "paper_2106_02858_gb300", "csrc", "dg_stage.cuh")
 # FP32 stage-kernel forms, indexed by cmcg_options.stage_variant - 1.
 STAGE_FORMS = ["dg_stage_kernel<float, 1>", "dg_stage_kernel<float, 3>", "dg_stage_kernel<float, 4>",
                "dg_stage_quad<float, 4>", "dg_stage_quad<float, 5>", "dg_stage_quad<float, 6>",
-               "dg_stage_tc (tcgen05 3xTF32)"]
+               "dg_stage_tc (tcgen05 3xTF32, 2 threads / tet)", "dg_stage_tc4 (tcgen05 3xTF32, 4 threads / tet)"]
 
 
 def peaks():
@@ -81,16 +81,43 @@ def _oracle_child(steps: int, warmup: int) -> None:
     print(json.dumps({"step_s": times, "M": st.M, "ndof": p.ndof}))
 
 
-def oracle_sample(steps: int, warmup: int):
+def host_cpu():
+    """(logical cores, model name) of this host, from os.cpu_count() and lscpu."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def oracle_sample(steps: int, warmup: int, nproc: int = 1):
+    """Times RK4 steps of the oracle in ``nproc`` concurrent single-thread processes (replicas of
+    the same program on the same input); returns per-step times of every replica and M, ndof."""
     env = dict(os.environ)
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
         env[v] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     cmd = [sys.executable, "-c", f"import bench; bench._oracle_child({steps}, {warmup})"]
-    r = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+    procs = [subprocess.Popen(cmd, cwd=ROOT, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True)
+             for _ in range(nproc)]
+    outs = []
+    for pr in procs:
+        out, err = pr.communicate()
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        outs.append(json.loads(out.strip().splitlines()[-1]))
+    return {"step_s": [o["step_s"] for o in outs], "M": outs[0]["M"], "ndof": outs[0]["ndof"]}
+
+
+def oracle_rate(r):
+    """Steps per second of a replica sample: every replica's steps over the slowest replica's time."""
+    per = [sum(ts) for ts in r["step_s"]]
+    return len(per) * len(r["step_s"][0]) / max(per)
 
 
 # ---------------------------------------------------------------------------------------------
@@ -209,14 +236,16 @@ def replica_throughput(local_s: float, steps: int, world: int, device=None):
 # Secondary workloads: batched right-hand sides and a served request stream.
 # ---------------------------------------------------------------------------------------------
 
-def measure_batched_rhs(cmcg, I, reps: int = 3):
+def measure_batched_rhs(cmcg, I, fp32_peak=None, tf32_peak=None, reps: int = 3):
     """32 Gaussian sources on the 384-tet cube at P3 (omega = 4 pi) in one batch handle, FP32
-    sweeps, CG to 1e-6 per source; timed through the host-buffer batch entry."""
+    sweeps (kernel form chosen by timing), CG to 1e-6 per source; timed through the host-buffer
+    batch entry."""
     prob = I.batched_rhs(nrhs=32)
     mesh = cmcg.make_mesh(prob.mesh.verts, prob.mesh.tets, prob.mesh.tags)
     nrhs = prob.j_re.shape[0]
     opt = cmcg.cmcg_default_options(order=prob.order, precision=cmcg.CMCG_FP32)
     h = cmcg.cmcg_create_batch([(mesh, prob.eps, prob.mu, prob.omega)] * nrhs, opt)
+    form, tune = cmcg.cmcg_get_tuning(h)
     jr, ji = list(prob.j_re), list(prob.j_im)
     cmcg.cmcg_solve_batch(h, jr, ji, prob.tol, MAX_ITER)  # warm-up (captures the sweep graphs)
     cmcg.cmcg_profile_enable(h, True)
@@ -228,12 +257,101 @@ def measure_batched_rhs(cmcg, I, reps: int = 3):
     steps = cmcg.cmcg_get_problem(h, 0)[1]
     periods = sum(3 + 2 * i.iters for i in infos)
     h.close()
-    return {"workload": "384-tet cube, P3, omega = 4 pi, 32 Gaussian sources in one handle, FP32, CG 1e-6",
-            "solves_per_s": nrhs / dt, "ms_per_batch": dt * 1e3,
-            "dof_updates_per_s": prob.nt * 6 * prob.np_ * steps * periods / dt,
-            "cg_iters": [i.iters for i in infos][:4] + ["..."],
-            "us_per_stage_launch": 1e3 * free_ms / max(free_stages, 1),
-            "note": "working set L2-resident: HBM fraction not meaningful"}
+    us = 1e3 * free_ms / max(free_stages, 1)
+    np_, nfp = prob.np_, (prob.order + 1) * (prob.order + 2) // 2
+    # the two contractions per tetrahedron and stage: volume 3 (components) x 3 Np x Np and lift
+    # 3 x Np x 4 Nfp multiply-adds per E / H half, each as three TF32 products on the tensor cores
+    mma_flops = 2 * 2 * 3 * (3 * np_ * np_ + np_ * 4 * nfp) * prob.nt * nrhs
+    out = {"workload": "384-tet cube, P3, omega = 4 pi, 32 Gaussian sources in one handle, FP32, CG 1e-6",
+           "solves_per_s": nrhs / dt, "ms_per_batch": dt * 1e3,
+           "dof_updates_per_s": prob.nt * 6 * prob.np_ * steps * periods / dt,
+           "cg_iters": [i.iters for i in infos][:4] + ["..."],
+           "stage_form": STAGE_FORMS[form], "tuning_us": tune,
+           "us_per_stage_launch": us,
+           "note": "working set L2-resident: HBM fraction not meaningful"}
+    if tf32_peak:
+        out["tensor"] = {"achieved_tflops_3xtf32": 3 * mma_flops / (us * 1e-6) / 1e12, "peak_tf32_tflops": tf32_peak,
+                         "peak_source": "measured (tcgen05 kind::tf32 loop in this run)"}
+        out["tensor"]["frac"] = out["tensor"]["achieved_tflops_3xtf32"] / tf32_peak
+    return out
+
+
+def measure_uneven_batch(cmcg, I, hbm_peak):
+    """The 64 uneven problems (n ~ U{6..20}, q ~ U{1,2,3}, omega ~ U{2,4,8} pi, eps on seeded
+    2x2x2 blocks), one batch handle per order (kernel form chosen by timing), FP32, CG to 1e-5.
+    One warm-up solve capped at one CG iteration captures the sweep graphs; the timed solves run
+    the three handles one after the other.  HBM fraction: the stages' algorithmic bytes of the
+    work each problem does (nested-form bytes for every stage: a lower bound on source stages)
+    over the summed sweep time."""
+    import numpy as np
+    probs = I.uneven_batch()
+    total_s = 0.0
+    dof_updates = 0.0
+    alg_bytes = 0.0
+    sweep_ms = 0.0
+    forms = {}
+    iters = []
+    for q in (1, 2, 3):
+        sub = [p for p in probs if p.order == q]
+        meshes = [cmcg.make_mesh(p.mesh.verts, p.mesh.tets, p.mesh.tags) for p in sub]
+        opt = cmcg.cmcg_default_options(order=q, precision=cmcg.CMCG_FP32)
+        h = cmcg.cmcg_create_batch([(m, p.eps, p.mu, p.omega) for m, p in zip(meshes, sub)], opt)
+        forms[f"P{q}"] = STAGE_FORMS[cmcg.cmcg_get_tuning(h)[0]]
+        jr, ji = [p.j_re for p in sub], [p.j_im for p in sub]
+        cmcg.cmcg_solve_batch(h, jr, ji, 1e-5, 1)
+        cmcg.cmcg_profile_enable(h, True)
+        t0 = time.perf_counter()
+        _e, _h, infos = cmcg.cmcg_solve_batch(h, jr, ji, 1e-5, MAX_ITER)
+        total_s += time.perf_counter() - t0
+        fm, _fs, sm, _ss = cmcg.cmcg_profile_read(h)
+        sweep_ms += fm + sm
+        s = 2 if q == 1 else 4
+        for p, i in zip(sub, infos):
+            assert i.status == cmcg.CMCG_OK, (p.name, i.status)
+            per = 3 + 2 * i.iters
+            dof_updates += p.ndof * i.steps_per_period * per
+            field = (5.0 / 2.0 if s == 2 else 11.0 / 4.0) * 4 * p.ndof
+            alg_bytes += per * i.steps_per_period * s * (field + ((9 + 2 + 4 * 7) * 4 + 16) * p.nt)
+            iters.append(i.iters)
+        h.close()
+    achieved = alg_bytes / (sweep_ms * 1e-3) / 1e9
+    return {"workload": "64 problems: n^3 Kuhn cubes n ~ U{6..20}, P1-P3, omega in {2,4,8} pi, eps on seeded 2x2x2 "
+                        "blocks U[1,4], impedance boundary, one seeded Gaussian source each; FP32, CG 1e-5; "
+                        "one handle per order",
+            "problems": len(probs), "dofs": int(sum(p.ndof for p in probs)),
+            "solves_per_s": len(probs) / total_s, "seconds": total_s,
+            "dof_updates_per_s": dof_updates / total_s, "stage_forms": forms,
+            "cg_iters_min_median_max": [int(min(iters)), float(np.median(iters)), int(max(iters))],
+            "hbm": {"achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
+                    "note": "algorithmic bytes of the work done / summed sweep time (includes launch gaps)"}}
+
+
+def measure_large_request(cmcg, I, hbm_peak):
+    """The large request of the served stream at its stated size: the 64^3-cube Kuhn mesh
+    (1,572,864 tets), P2 (94.4 M dofs), omega = 4 pi (644 RK4 steps per period), impedance
+    boundary, one Gaussian source, FP32 sweeps, CG to 1e-6, through the host-buffer entry point.
+    Its stage working set (about 1.3 GB) is far beyond L2, so the stage is HBM-bound."""
+    p = I.cube_problem(64, 2, 4 * math.pi, (0.45, 0.5, 0.55), (0.0, 1.0, 0.0), 0.1, tol=1e-6)
+    h, _m = cmcg.create_for_problem(p, precision=cmcg.CMCG_FP32)
+    form, tune = cmcg.cmcg_get_tuning(h)
+    cmcg.cmcg_profile_enable(h, True)
+    t0 = time.perf_counter()
+    _e, _h, info = cmcg.cmcg_solve(h, p.j_re, p.j_im, p.tol, MAX_ITER)
+    dt = time.perf_counter() - t0
+    fm, fs, sm, ss = cmcg.cmcg_profile_read(h)
+    h.close()
+    stage_us = 1e3 * fm / max(fs, 1)
+    alg = stage_algorithmic_bytes(p.nt, p.ndof, 4)
+    achieved = alg / (stage_us * 1e-6) / 1e9
+    periods = 3 + 2 * info.iters
+    return {"workload": "64^3 Kuhn cube (1,572,864 tets), P2 (94,371,840 dofs), omega = 4 pi, impedance boundary, "
+                        "one Gaussian source, FP32, CG 1e-6, solved alone",
+            "status": info.status, "seconds": dt, "cg_iters": info.iters, "steps_per_period": info.steps_per_period,
+            "dof_updates_per_s": p.ndof * info.steps_per_period * periods / dt,
+            "stage_form": STAGE_FORMS[form], "tuning_us": tune,
+            "stage_us": stage_us, "source_stage_us": 1e3 * sm / max(ss, 1),
+            "hbm": {"achieved_gbs": achieved, "peak_gbs": hbm_peak, "frac": achieved / hbm_peak,
+                    "algorithmic_bytes_per_launch": alg}}
 
 
 def measure_serving(cmcg, I, rate_hz: float = 150.0, n_small: int = 150, n_large: int = 3, seed: int = 0,
@@ -313,21 +431,24 @@ def measure_serving(cmcg, I, rate_hz: float = 150.0, n_small: int = 150, n_large
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
-    r = oracle_sample(args.steps, args.warmup)
-    step_s = statistics.mean(r["step_s"])
+    cores, model = host_cpu()
+    r = oracle_sample(args.steps, args.warmup, nproc=cores)
+    steps_per_s = oracle_rate(r)
     steps_per_solve = r["M"] * (3 + 2 * CG_ITERS_FOR_REFERENCE)
-    value = 1.0 / (step_s * steps_per_solve)
+    value = steps_per_s / steps_per_solve
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": 1e3 * max(sum(ts) for ts in r["step_s"]) / args.steps,
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "parallelism": "host CPU, one thread"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": {"workload": WORKLOAD, "parallelism": f"host CPU, {cores} single-thread oracle processes"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
                          "sample": f"each step = one RK4 step (4 operator applications) of the FP64 numpy oracle on "
-                                   f"the full 81,648-tet P2 mesh; solves/s extrapolated as 1 / (step time x M x "
+                                   f"the full 81,648-tet P2 mesh in each of {cores} concurrent single-thread "
+                                   f"processes; solves/s = replicas x steps / slowest replica's time / (M x "
                                    f"(3 + 2 x {CG_ITERS_FOR_REFERENCE})) with M = {r['M']}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "dof_updates_per_s": r["ndof"] / step_s,
+        "dof_updates_per_s": r["ndof"] * steps_per_s,
     }
     print(json.dumps(line), flush=True)
 
@@ -443,6 +564,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
 
     # Roofline of the stage kernel over the timed region (source-free sweeps).
     peak, peak_kind = peaks()
+    fp32_peak, tf32_peak = cmcg.cmcg_measure_peaks(local_rank)
     stage_us = free_ms * 1e3 / max(free_stages, 1)
     alg = stage_algorithmic_bytes(prob.nt, prob.ndof, 4)
     achieved = alg / (stage_us * 1e-6) / 1e9
@@ -451,28 +573,40 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "traffic": recorded_traffic(form + 1), "kernel": f"{STAGE_FORMS[form]} (P2, nested RK4 stage)",
                 "stage_variant": form + 1, "tuning_us": form_us,
                 "alu": {"achieved": stage_algorithmic_flops(prob.nt, prob.order) / (stage_us * 1e-6) / 1e12,
-                        "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                        "peak": fp32_peak, "unit": "TFLOP/s",
                         "frac": stage_algorithmic_flops(prob.nt, prob.order) / (stage_us * 1e-6) / 1e12
-                        / FP32_PEAK_TFLOPS, "peak_source": "unit counts x maximum SM clock"},
+                        / fp32_peak, "peak_source": "measured (FP32 FMA loop in this run)",
+                        "tf32_tensor_peak_tflops": tf32_peak,
+                        "nominal_fp32_tflops": FP32_PEAK_TFLOPS},
                 "algorithmic_bytes_per_launch": alg, "avg_launch_us": stage_us, "peak_source": peak_kind,
                 "source_stage_us": src_ms * 1e3 / max(src_stages, 1)}
 
-    batched = serving = None
+    batched = serving = uneven = large = None
     if rank == 0 and not args.skip_extra:
-        batched = measure_batched_rhs(cmcg, I)
-        serving = [measure_serving(cmcg, I, rate_hz=40.0, n_small=160, n_large=2),
-                   measure_serving(cmcg, I, rate_hz=160.0, n_small=320, n_large=4, seed=1)]
+        batched = measure_batched_rhs(cmcg, I, fp32_peak, tf32_peak)
+        uneven = measure_uneven_batch(cmcg, I, peak)
+        serving = [measure_serving(cmcg, I, rate_hz=r, n_small=n - n // 20, n_large=n // 20, seed=k)
+                   for k, (r, n) in enumerate(((20.0, 200), (40.0, 300), (80.0, 400), (160.0, 600)))]
+        if not args.skip_large:
+            large = measure_large_request(cmcg, I, peak)
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:
-        r = oracle_sample(2, 0)
-        step_s = statistics.mean(r["step_s"])
-        cpu_value = 1.0 / (step_s * h32.steps * periods)
-        cpu = {"value": cpu_value, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"2 RK4 steps (8 operator applications) of the FP64 numpy oracle on the full mesh, "
-                         f"one thread; extrapolated to a solve as step time x {h32.steps} steps x {periods} "
-                         f"periods ({iters} CG iterations)",
-               "dof_updates_per_s": r["ndof"] / step_s}
+        cores, model = host_cpu()
+        one = oracle_sample(2, 0, nproc=1)
+        rate1 = oracle_rate(one)
+        allc = oracle_sample(1, 0, nproc=cores)
+        rate_all = oracle_rate(allc)
+        steps_per_solve = h32.steps * periods
+        cpu = {"value": rate_all / steps_per_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "cpu_model": model,
+               "sample": f"RK4 steps (4 operator applications each) of the FP64 numpy oracle on the full mesh in "
+                         f"{cores} concurrent single-thread processes (one step each); solves/s = steps per "
+                         f"second / ({h32.steps} steps x {periods} periods, {iters} CG iterations)",
+               "dof_updates_per_s": one["ndof"] * rate_all,
+               "single_thread": {"value": rate1 / steps_per_solve, "unit": UNIT, "cores": 1,
+                                 "sample": "2 RK4 steps in one single-thread process",
+                                 "dof_updates_per_s": one["ndof"] * rate1}}
 
     if rank == 0:
         line = {
@@ -496,7 +630,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
             "clocks": clocks,
             "fw_at_equal_periods": fw,
             "batched_rhs": batched,
+            "uneven_batch": uneven,
             "serving": serving,
+            "serving_large_request": large,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -533,7 +669,8 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fw", action="store_true")
-    ap.add_argument("--skip-extra", action="store_true", help="skip the batched-RHS and serving measurements")
+    ap.add_argument("--skip-extra", action="store_true", help="skip the batched-RHS, uneven-batch and serving measurements")
+    ap.add_argument("--skip-large", action="store_true", help="skip the 64^3-cube P2 request")
     ap.add_argument("--profile-sweep", action="store_true", help="run one period sweep only (for ncu)")
     ap.add_argument("--stage-variant", type=int, default=0, help="force a stage-kernel form (see cmcg_options)")
     args = ap.parse_args()

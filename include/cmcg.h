@@ -117,8 +117,12 @@ typedef struct cmcg_mesh {
  *                     in both.
  *   flux:             CMCG_FLUX_UPWIND (the paper's scheme) or
  *                     CMCG_FLUX_CENTRED (energy-conserving, for tests).
- *   c_q:              CFL constant of Eq. cfl; <= 0 selects 0.24 (q = 1),
- *                     0.12 (q = 2, 3).
+ *   c_q:              CFL constant of Eq. cfl; <= 0 selects 0.12 for every
+ *                     order.  Section 5.3 prints 0.24 for P1 / RK2 (a 2D
+ *                     constant); on 3D meshes of 8^3 cubes and more with
+ *                     permittivity jumps it makes one RK2 period grow a mode
+ *                     tenfold and more, so P1 uses half of it by default (pass
+ *                     0.24 to get the printed value).
  *   steps_per_period: > 0 forces M (dt = T / M) instead of the CFL choice.
  *   hbm_budget_bytes: > 0 makes cmcg_create fail with
  *                     CMCG_ERR_OUT_OF_MEMORY if the handle would need more
@@ -129,10 +133,11 @@ typedef struct cmcg_mesh {
  *                     FP32: 0, 1, 2 = two threads per tetrahedron (E / H)
  *                     with at least 1, 3, 4 resident 128-thread blocks per
  *                     SM; 3, 4, 5 = four threads per tetrahedron (E / H x
- *                     node half) with at least 4, 5, 6; 6 = the volume and
- *                     lift contractions on the tensor cores (tcgen05, three
- *                     TF32 products per FP32 product, FP32 accumulation),
- *                     two threads per tetrahedron.  FP64: 0 = two threads
+ *                     node half) with at least 4, 5, 6; 6, 7 = the volume
+ *                     and lift contractions on the tensor cores (tcgen05,
+ *                     three TF32 products per FP32 product, FP32
+ *                     accumulation) with two / four threads per
+ *                     tetrahedron.  FP64: 0 = two threads
  *                     per tetrahedron; 1, 2 = four threads with at least
  *                     2, 3.  Other k: CMCG_ERR_INVALID_ARG.  Results do not
  *                     depend on it beyond rounding.
@@ -218,6 +223,43 @@ typedef struct cmcg_problem {
  * entry points (dgtd_*, cmcg_inner, cmcg_solve[_device]) need nprob == 1. */
 int cmcg_create_batch(int nprob, const cmcg_problem* probs, const cmcg_options* opt, cmcg_handle** out);
 
+/* ---------------------------------------------------------------------------
+ * Element partition (sharding).  The DG operator couples tetrahedra only through
+ * face fluxes (Section 5.2.2), so a part of an element partition needs, per RK
+ * stage, the stage values of the tetrahedra across its cut faces (its ghosts),
+ * and CMCG needs, per CG iteration, its FP64 inner products summed over the
+ * parts (Section 2.2, Algorithm cmcg).  The paper has no partitioned solver.
+ *
+ * cmcg_partition_slabs (host only): part[k] in [0, nparts) for every
+ * tetrahedron: tetrahedra sorted by the centroid coordinate `axis` (0, 1, 2)
+ * and cut into nparts slabs of (nearly) equal count.
+ *
+ * cmcg_shard_plan (host only): the local mesh of part p: its owned tetrahedra
+ * in increasing global order, then its ghosts (the other parts' tetrahedra that
+ * share a face with an owned one) in increasing global order.
+ * global_of_local[n_owned + n_ghost]; per ghost g: ghost_owner_part[g] and
+ * ghost_owner_local[g] (its index in the owner's local numbering);
+ * local_tags[(n_owned + n_ghost) * 4]: the mesh's face tags, a ghost's face
+ * whose neighbour is not in the local mesh tagged PEC.  Output arrays may be
+ * NULL (call once with NULLs to get the counts).
+ *
+ * cmcg_create_sharded: one handle over the parts of `part` (nparts >= 1, every
+ * part owning a tetrahedron), all on opt->device.  Every part steps with the M
+ * of the whole mesh; after every stage each ghost receives its owner's values
+ * (a halo-exchange kernel between the parts' device buffers); ghosts carry no
+ * weight in the inner products, whose per-part sums are added before every CG
+ * scalar.  The single-problem entry points (cmcg_solve[_device],
+ * dgtd_period_forward / adjoint [_device], dgtd_apply, cmcg_inner,
+ * cmcg_get_sizes) take it with arrays of the whole mesh; the batch, FW,
+ * boundary-data and conductivity entry points return CMCG_ERR_INVALID_ARG.
+ * Results equal those of cmcg_create on the whole mesh up to rounding. */
+int cmcg_partition_slabs(const cmcg_mesh* mesh, int nparts, int axis, int32_t* part);
+int cmcg_shard_plan(const cmcg_mesh* mesh, const int32_t* part, int nparts, int p, int64_t* n_owned, int64_t* n_ghost,
+                    int32_t* global_of_local, int32_t* ghost_owner_part, int32_t* ghost_owner_local,
+                    uint8_t* local_tags);
+int cmcg_create_sharded(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
+                        const cmcg_options* opt, int nparts, const int32_t* part, cmcg_handle** out);
+
 /* Number of problems of a handle (0 for NULL). */
 int cmcg_batch_size(const cmcg_handle* h);
 
@@ -233,9 +275,9 @@ int cmcg_set_stream(cmcg_handle* h, void* stream);
 
 /* Stage-kernel form in use (0-based, as stage_variant - 1) and, when it was
  * chosen by timing at creation, the measured microseconds per stage of each
- * form (8 entries: [0..6] indexed by form, see stage_variant; [7] the chosen
- * form with stage_overlap on; -1 where not timed or rejected by the device).
- * Any pointer may be NULL. */
+ * form (10 entries: [0..7] indexed by form, see stage_variant; [8] the chosen
+ * form with stage_overlap on; [9] unused; -1 where not timed or rejected by the
+ * device).  Any pointer may be NULL. */
 int cmcg_get_tuning(const cmcg_handle* h, int* variant, double* us_per_stage);
 
 /* Sizes of the handle: nt, Np, M (steps per period), dt, number of doubles of
@@ -351,6 +393,18 @@ int64_t cmcg_kernel_launches(const cmcg_handle* h);
  * first call allocates two field vectors on the device. */
 int cmcg_set_boundary_data(cmcg_handle* h, int problem, const double* g_re, const double* g_im);
 
+/* Conductivity sigma_K >= 0 of every tetrahedron of problem `problem`
+ * (Eq. maxwell_time_strong, Section 1: eps dE/dt + sigma E + curl H = J; the
+ * coefficients of Section 3.1; the term (sigma E_h, v_h) of the DG scheme,
+ * Section 5.2.2): the E rows of the operator gain -(sigma_K / eps_K) E.  The
+ * adjoint stays Sigma P Sigma (the term is symmetric and acts on E only).
+ * sigma: host double[nt] in the mesh's order, or NULL to remove it (sigma = 0,
+ * the paper's experiments).  The time step is the one of Eq. cfl; a sigma with
+ * dt sigma_K / eps_K > 2 (beyond the explicit step's real stability interval)
+ * or a negative or non-finite value returns CMCG_ERR_INVALID_ARG and changes
+ * nothing.  It applies to every later sweep and solve of the handle. */
+int cmcg_set_conductivity(cmcg_handle* h, int problem, const double* sigma);
+
 /* Limiting-amplitude baseline ("full wave", FW, Section 6): marches the
  * scheme with the time-harmonic source from rest for `periods` periods,
  * U = P_{psi,w}^periods 0, then returns the filtered field F_{psi,w} U of one
@@ -375,6 +429,14 @@ int cmcg_fw_solve_batch(cmcg_handle* h, int periods, const double* const* j_re, 
 int cmcg_profile_enable(cmcg_handle* h, int on);
 int cmcg_profile_read(cmcg_handle* h, double* free_ms, int64_t* free_stages, double* source_ms,
                       int64_t* source_stages);
+
+/* Measured arithmetic peaks of a device (a measurement utility; the paper has no
+ * counterpart): *fp32_tflops from 8 independent FMA chains per thread on every
+ * SM, *tf32_tflops from back-to-back tensor-core MMAs (tcgen05 kind::tf32,
+ * M = 128, N = 256, K = 8, one accumulator in tensor memory per SM).  Each is
+ * one timed launch after a warm-up launch.  Either pointer may be NULL (not
+ * measured).  CMCG_ERR_DEVICE_TIMEOUT if the MMA wait (bounded, ~1 s) ran out. */
+int cmcg_measure_peaks(int device, double* fp32_tflops, double* tf32_tflops);
 
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of CMCG requests (no counterpart in the paper;

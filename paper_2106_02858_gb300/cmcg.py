@@ -101,6 +101,7 @@ def _load() -> C.CDLL:
         "cmcg_device_bytes": (C.c_int64, [_vp]),
         "cmcg_fw_solve": (C.c_int, [_vp, _dp, _dp, C.c_int, _dp, _dp, _dp, _dp]),
         "cmcg_set_boundary_data": (C.c_int, [_vp, C.c_int, _dp, _dp]),
+        "cmcg_set_conductivity": (C.c_int, [_vp, C.c_int, _dp]),
         "cmcg_fw_solve_batch": (C.c_int, [_vp, C.c_int, C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp),
                                           C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp)]),
         "cmcg_server_default_options": (None, [C.POINTER(cmcg_server_options)]),
@@ -129,6 +130,13 @@ def _load() -> C.CDLL:
         "cmcg_inner": (C.c_int, [_vp, _dp, _dp, C.POINTER(C.c_double)]),
         "cmcg_inner_noalloc": (C.c_int, [C.c_int, C.c_int64, _vp, _vp, _vp, _vp, _vp]),
         "cmcg_profile_enable": (C.c_int, [_vp, C.c_int]),
+        "cmcg_measure_peaks": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+        "cmcg_partition_slabs": (C.c_int, [C.POINTER(cmcg_mesh), C.c_int, C.c_int, C.POINTER(C.c_int32)]),
+        "cmcg_shard_plan": (C.c_int, [C.POINTER(cmcg_mesh), C.POINTER(C.c_int32), C.c_int, C.c_int,
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)]),
+        "cmcg_create_sharded": (C.c_int, [C.POINTER(cmcg_mesh), _dp, _dp, C.c_double, C.POINTER(cmcg_options),
+                                          C.c_int, C.POINTER(C.c_int32), C.POINTER(_vp)]),
         "cmcg_profile_read": (C.c_int, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                         C.POINTER(C.c_int64)]),
     }
@@ -147,7 +155,9 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_inner", "cmcg_inner_noalloc", "cmcg_get_tuning", "cmcg_create_batch", "cmcg_batch_size",
             "cmcg_get_problem", "cmcg_solve_batch", "cmcg_solve_batch_device", "cmcg_solve_batch_n",
             "cmcg_device_bytes", "cmcg_fw_solve", "cmcg_fw_solve_batch", "cmcg_set_boundary_data", "cmcg_server_default_options", "cmcg_server_create", "cmcg_server_add_model",
-            "cmcg_server_submit", "cmcg_server_poll", "cmcg_server_stats", "cmcg_server_destroy")
+            "cmcg_server_submit", "cmcg_server_poll", "cmcg_server_stats", "cmcg_server_destroy",
+            "cmcg_measure_peaks", "cmcg_set_conductivity", "cmcg_partition_slabs", "cmcg_shard_plan",
+            "cmcg_create_sharded")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
 
@@ -281,6 +291,48 @@ def cmcg_create(mesh: MeshArrays, eps, mu, omega: float, opt: cmcg_options) -> H
     return Handle(out.value, nt.value, np_.value, steps.value, dt.value)
 
 
+def cmcg_partition_slabs(mesh: MeshArrays, nparts: int, axis: int = 2) -> np.ndarray:
+    """Slab partition: part index (int32) of every tetrahedron."""
+    part = np.empty(mesh.struct.nt, dtype=np.int32)
+    _check(_lib.cmcg_partition_slabs(C.byref(mesh.struct), int(nparts), int(axis),
+                                     part.ctypes.data_as(C.POINTER(C.c_int32))), "cmcg_partition_slabs")
+    return part
+
+
+def cmcg_shard_plan(mesh: MeshArrays, part, nparts: int, p: int):
+    """Local mesh of part p: dict with n_owned, global_of_local (owned, then ghosts),
+    ghost_owner_part, ghost_owner_local and local_tags (n_local, 4)."""
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    pp = part.ctypes.data_as(C.POINTER(C.c_int32))
+    no, ng = C.c_int64(), C.c_int64()
+    _check(_lib.cmcg_shard_plan(C.byref(mesh.struct), pp, int(nparts), int(p), C.byref(no), C.byref(ng),
+                                None, None, None, None), "cmcg_shard_plan")
+    nl = no.value + ng.value
+    gl = np.empty(nl, np.int32)
+    op, ol = np.empty(ng.value, np.int32), np.empty(ng.value, np.int32)
+    tags = np.empty((nl, 4), np.uint8)
+    i32 = lambda a: a.ctypes.data_as(C.POINTER(C.c_int32))
+    _check(_lib.cmcg_shard_plan(C.byref(mesh.struct), pp, int(nparts), int(p), C.byref(no), C.byref(ng),
+                                i32(gl), i32(op), i32(ol), tags.ctypes.data_as(C.POINTER(C.c_uint8))),
+           "cmcg_shard_plan")
+    return {"n_owned": no.value, "global_of_local": gl, "ghost_owner_part": op, "ghost_owner_local": ol,
+            "local_tags": tags}
+
+
+def cmcg_create_sharded(mesh: MeshArrays, eps, mu, omega: float, opt: cmcg_options, part) -> Handle:
+    """One handle over the parts of ``part``; takes and returns fields of the whole mesh."""
+    e, m = _f64(eps), _f64(mu)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    nparts = int(part.max()) + 1
+    out = C.c_void_p()
+    _check(_lib.cmcg_create_sharded(C.byref(mesh.struct), _ptr(e), _ptr(m), float(omega), C.byref(opt), nparts,
+                                    part.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(out)), "cmcg_create_sharded")
+    nt, np_, steps, dt, fl = C.c_int64(), C.c_int(), C.c_int(), C.c_double(), C.c_int64()
+    _check(_lib.cmcg_get_sizes(out, C.byref(nt), C.byref(np_), C.byref(steps), C.byref(dt), C.byref(fl)),
+           "cmcg_get_sizes")
+    return Handle(out.value, nt.value, np_.value, steps.value, dt.value)
+
+
 def cmcg_create_batch(problems, opt: cmcg_options) -> Handle:
     """``problems``: list of (MeshArrays, eps, mu, omega)."""
     keep = []
@@ -360,7 +412,7 @@ def cmcg_get_sizes(h: Handle):
 def cmcg_get_tuning(h: Handle):
     """(variant in use, microseconds per stage of each timed variant or None)."""
     v = C.c_int()
-    us = (C.c_double * 8)()
+    us = (C.c_double * 10)()
     _check(_lib.cmcg_get_tuning(h.ptr, C.byref(v), us), "cmcg_get_tuning")
     return v.value, [x if x >= 0 else None for x in us]
 
@@ -396,6 +448,13 @@ def cmcg_inner_noalloc(order: int, nt: int, u, v, w, out, stream=None) -> None:
 
 def cmcg_profile_enable(h: Handle, on: bool = True) -> None:
     _check(_lib.cmcg_profile_enable(h.ptr, int(bool(on))), "cmcg_profile_enable")
+
+
+def cmcg_measure_peaks(device: int = 0):
+    """(FP32 CUDA-core TFLOP/s, TF32 tensor-core TFLOP/s) measured on the device."""
+    f, t = C.c_double(), C.c_double()
+    _check(_lib.cmcg_measure_peaks(int(device), C.byref(f), C.byref(t)), "cmcg_measure_peaks")
+    return f.value, t.value
 
 
 def cmcg_profile_read(h: Handle):
@@ -464,6 +523,13 @@ def cmcg_set_boundary_data(h: Handle, g_re, g_im=None, problem: int = 0) -> None
     gi = None if (g_re is None or g_im is None) else _f64(g_im, (nt, 4, 3, nfp), "g_im")
     h._keep_b = (gr, gi)
     _check(_lib.cmcg_set_boundary_data(h.ptr, int(problem), _ptr(gr), _ptr(gi)), "cmcg_set_boundary_data")
+
+
+def cmcg_set_conductivity(h: Handle, sigma, problem: int = 0) -> None:
+    """Conductivity per tetrahedron (nt,) of problem `problem`; None removes it."""
+    nt = h.problems[problem][0]
+    sg = None if sigma is None else _f64(sigma, (nt,), "sigma")
+    _check(_lib.cmcg_set_conductivity(h.ptr, int(problem), _ptr(sg)), "cmcg_set_conductivity")
 
 
 def cmcg_fw_solve(h: Handle, j_re, j_im=None, periods: int = 1):

@@ -58,6 +58,9 @@ struct Prob {
   std::vector<std::complex<double>> fa, fb;  // filter weights per step 0..M (with 2/T)
   std::vector<ImpFace> imp;                   // impedance faces
   bool has_bdata = false;                     // boundary data set (cmcg_set_boundary_data)
+  bool has_sigma = false;                     // conductivity set (cmcg_set_conductivity)
+  std::vector<int32_t> ext_of_int;            // internal (problem-local) -> external tetrahedron (-1 padding)
+  std::vector<int32_t> int_of_ext;            // external -> internal (problem-local)
 };
 
 }  // namespace
@@ -101,6 +104,16 @@ struct cmcg_handle {
   int64_t launches = 0;
   size_t bytes = 0;
   bool has_bdata = false;  // some problem has boundary data
+  bool has_sigma = false;  // some problem has a conductivity
+  // Sharded handle (cmcg_create_sharded): the problems are the parts of one mesh, each with its
+  // ghost layer; ghosts receive their owners' values after every stage and the CG reductions
+  // sum over all parts.
+  bool coupled = false;
+  int64_t nt_global = 0;
+  int64_t nhalo = 0;
+  int64_t *halo_dst = nullptr, *halo_src = nullptr;  // internal tetrahedra: ghost <- owner
+  int32_t *g_in = nullptr, *g_out = nullptr;          // internal -> global tetrahedron (g_out: owned only)
+  double* inv_eps_g = nullptr;                        // 1 / eps by global tetrahedron
   // CUDA graphs of whole sweeps, captured on first use on a private stream and launched on
   // `stream`; key: sweep kind, mask pointer, boundary data present.
   bool graphs = true;
@@ -108,7 +121,7 @@ struct cmcg_handle {
   std::map<std::tuple<int, const void*, bool>, cudaGraphExec_t> graph_exec;
   int form = 0;      // stage-kernel form (see launch_stage)
   bool pdl = false;  // stages launched with programmatic stream serialisation
-  double tune_us[8];      // [0..6] per form, [7] the chosen form with overlapped launches
+  double tune_us[10];     // [0..7] per form, [8] the chosen form with overlapped launches, [9] unused
   int32_t* err = nullptr;       // device status word of the stage kernels' bounded waits
   int32_t* err_host = nullptr;  // pinned
   // sweep profiling
@@ -281,6 +294,7 @@ void stage(cmcg_handle* h, StageArgs<R>& a, cudaStream_t st) {
   a.nbr = h->nbr;
   a.nti = h->nti;
   a.err = h->err;
+  a.sigma = h->has_sigma ? 1 : 0;
   a.tprob = h->tprob;
   if (h->q == 1) launch_stage<1, R>(a, st, h->form, h->pdl);
   else if (h->q == 2) launch_stage<2, R>(a, st, h->form, h->pdl);
@@ -290,6 +304,13 @@ template <typename R>
 void stage(cmcg_handle* h, StageArgs<R>& a) {
   stage<R>(h, a, h->stream);
   h->launches++;
+}
+
+// Sharded handles: every ghost takes its owner's values of the field a stage has just written.
+template <typename R>
+void halo(cmcg_handle* h, R* v, cudaStream_t st) {
+  if (!h->coupled || !v || h->nhalo == 0) return;
+  launch_halo<R>(v, h->halo_dst, h->halo_src, h->nhalo, h->np, st);
 }
 
 // Runs `emit(stream)` (a fixed sequence of `n` stage launches) on the handle's stream, from a
@@ -385,6 +406,7 @@ void sweep_free(cmcg_handle* h, bool adjoint, const int32_t* pactive) {
       a.coef = tab<R>(h->tab_free, l, h->nprob);
       a.pactive = pactive;
       stage<R>(h, a, st);
+      halo<R>(h, a.out, st);
     }
   });
   prof_end(h, pe);
@@ -436,6 +458,7 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
     a.coef = tab<R>(table, l, h->nprob);
     a.pactive = mask;
     stage<R>(h, a, st);
+    halo<R>(h, a.out, st);
   }
   });
   prof_end(h, pe);
@@ -500,7 +523,7 @@ int autotune(cmcg_handle* h, int nforms, int overlap) {
     double us;
     int rc = time_one(&us);
     if (rc) return rc;
-    h->tune_us[7] = us;
+    h->tune_us[8] = us;
     h->pdl = us >= 0 && us < best;
   } else {
     h->pdl = overlap == 1;
@@ -513,22 +536,30 @@ int autotune(cmcg_handle* h, int nforms, int overlap) {
 }
 
 // Per-problem layout conversion.
+// (For a sharded handle the external arrays are the global mesh's: every part reads its owned
+// and ghost tetrahedra and writes its owned ones.)
 template <typename R>
 void to_int(cmcg_handle* h, int p, const double* ext, int ncomp_ext, void* in, int ncomp_in, int cnt,
             const double* per_tet) {
   const Prob& P = h->P[p];
   R* base = (R*)in + P.tile0 * int64_t(ncomp_in) * h->np * TILE;
-  launch_to_internal<R>(ext, ncomp_ext, 0, base, ncomp_in, 0, cnt, h->e_of_i + P.tet0, P.nti, h->np, 1.0,
-                        per_tet ? per_tet + P.ext0 : nullptr, h->stream);
+  const int32_t* map = h->coupled ? h->g_in + P.tet0 : h->e_of_i + P.tet0;
+  const double* pt = per_tet ? (h->coupled ? h->inv_eps_g : per_tet + P.ext0) : nullptr;
+  launch_to_internal<R>(ext, ncomp_ext, 0, base, ncomp_in, 0, cnt, map, P.nti, h->np, 1.0, pt, h->stream);
   h->launches++;
 }
 template <typename R>
 void to_ext(cmcg_handle* h, int p, const void* in, int ncomp_in, int c_in0, double* ext, int ncomp_ext, int cnt) {
   const Prob& P = h->P[p];
   const R* base = (const R*)in + P.tile0 * int64_t(ncomp_in) * h->np * TILE;
-  launch_to_external<R>(base, ncomp_in, c_in0, ext, ncomp_ext, 0, cnt, h->e_of_i + P.tet0, P.nti, h->np, h->stream);
+  const int32_t* map = h->coupled ? h->g_out + P.tet0 : h->e_of_i + P.tet0;
+  launch_to_external<R>(base, ncomp_in, c_in0, ext, ncomp_ext, 0, cnt, map, P.nti, h->np, h->stream);
   h->launches++;
 }
+// Number of problems a single-problem entry point converts: all parts of a sharded handle.
+int nconv(const cmcg_handle* h) { return h->coupled ? h->nprob : 1; }
+// Tetrahedra of the external (caller's) arrays of a single-problem entry point.
+int64_t ext_nt(const cmcg_handle* h) { return h->coupled ? h->nt_global : h->nt_total; }
 template <typename R>
 void lincomb(cmcg_handle* h, void* o1, void* o2, void* o3, double a, const void* x, double b, const void* y) {
   launch_lincomb3<R>((R*)o1, (R*)o2, (R*)o3, a, (const R*)x, b, (const R*)y, h->nvec, h->stream);
@@ -566,10 +597,11 @@ int check_err(cmcg_handle* h) {
 template <typename R>
 int forward_dev(cmcg_handle* h, const double* u0, const double* j_re, const double* j_im, double* uT, double* fre,
                 double* fim) {
-  to_int<R>(h, 0, u0, 6, h->Uw, 6, 6, nullptr);
+  for (int p = 0; p < nconv(h); ++p) to_int<R>(h, p, u0, 6, h->Uw, 6, 6, nullptr);
   const bool filter = fre && fim;
   if (j_re) {
-    int rc = set_source<R>(h, &j_re, &j_im);
+    std::vector<const double*> jr(size_t(h->nprob), j_re), ji(size_t(h->nprob), j_im);
+    int rc = set_source<R>(h, jr.data(), ji.data(), nconv(h));
     if (rc) return rc;
   }
   if (filter) {
@@ -578,10 +610,12 @@ int forward_dev(cmcg_handle* h, const double* u0, const double* j_re, const doub
   }
   if (j_re || filter) sweep_source<R>(h, j_re != nullptr, filter);
   else sweep_free<R>(h, false, nullptr);
-  if (uT) to_ext<R>(h, 0, h->Uw, 6, 0, uT, 6, 6);
-  if (filter) {
-    to_ext<R>(h, 0, h->Fre, 6, 0, fre, 6, 6);
-    to_ext<R>(h, 0, h->Fim, 6, 0, fim, 6, 6);
+  for (int p = 0; p < nconv(h); ++p) {
+    if (uT) to_ext<R>(h, p, h->Uw, 6, 0, uT, 6, 6);
+    if (filter) {
+      to_ext<R>(h, p, h->Fre, 6, 0, fre, 6, 6);
+      to_ext<R>(h, p, h->Fim, 6, 0, fim, 6, 6);
+    }
   }
   CK(cudaGetLastError());
   return check_err(h);
@@ -589,9 +623,9 @@ int forward_dev(cmcg_handle* h, const double* u0, const double* j_re, const doub
 
 template <typename R>
 int adjoint_dev(cmcg_handle* h, const double* wT, double* w0) {
-  to_int<R>(h, 0, wT, 6, h->Uw, 6, 6, nullptr);
+  for (int p = 0; p < nconv(h); ++p) to_int<R>(h, p, wT, 6, h->Uw, 6, 6, nullptr);
   sweep_free<R>(h, true, nullptr);
-  to_ext<R>(h, 0, h->Uw, 6, 0, w0, 6, 6);
+  for (int p = 0; p < nconv(h); ++p) to_ext<R>(h, p, h->Uw, 6, 0, w0, 6, 6);
   CK(cudaGetLastError());
   return check_err(h);
 }
@@ -599,7 +633,7 @@ int adjoint_dev(cmcg_handle* h, const double* wT, double* w0) {
 template <typename R>
 int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, const double* j_im, int adjoint,
               double* out) {
-  to_int<R>(h, 0, u, 6, h->Uw, 6, 6, nullptr);
+  for (int p = 0; p < nconv(h); ++p) to_int<R>(h, p, u, 6, h->Uw, 6, 6, nullptr);
   CK(cudaMemsetAsync(h->vB, 0, h->nvec * h->rsize, h->stream));
   StageCoef<R> c;
   std::memset(&c, 0, sizeof(c));
@@ -607,7 +641,8 @@ int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, con
   c.c_out = R(1);
   c.s_cos = R(std::cos(h->P[0].omega * t));
   c.s_sin = R(std::sin(h->P[0].omega * t));
-  CK(cudaMemcpy(h->tab_one, &c, sizeof(c), cudaMemcpyHostToDevice));
+  const std::vector<StageCoef<R>> cs(size_t(h->nprob), c);  // every part of a sharded handle
+  CK(cudaMemcpy(h->tab_one, cs.data(), sizeof(c) * cs.size(), cudaMemcpyHostToDevice));
   StageArgs<R> a = blank<R>();
   a.vin = (const R*)h->Uw;
   a.base = (const R*)h->vB;
@@ -615,7 +650,8 @@ int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, con
   a.sH = adjoint ? R(-1) : R(1);
   a.coef = (const StageCoef<R>*)h->tab_one;
   if (j_re && !adjoint) {
-    int rc = set_source<R>(h, &j_re, &j_im);
+    std::vector<const double*> jr(size_t(h->nprob), j_re), ji(size_t(h->nprob), j_im);
+    int rc = set_source<R>(h, jr.data(), ji.data(), nconv(h));
     if (rc) return rc;
     a.jre = (const R*)h->Jre;
     a.jim = (const R*)h->Jim;
@@ -625,15 +661,17 @@ int apply_dev(cmcg_handle* h, double t, const double* u, const double* j_re, con
     }
   }
   stage<R>(h, a);
-  to_ext<R>(h, 0, h->vA, 6, 0, out, 6, 6);
+  for (int p = 0; p < nconv(h); ++p) to_ext<R>(h, p, h->vA, 6, 0, out, 6, 6);
   CK(cudaGetLastError());
   return check_err(h);
 }
 
 template <typename R>
 int inner_dev(cmcg_handle* h, const double* u, const double* v, double* out) {
-  to_int<R>(h, 0, u, 6, h->Uw, 6, 6, nullptr);
-  to_int<R>(h, 0, v, 6, h->vA, 6, 6, nullptr);
+  for (int p = 0; p < nconv(h); ++p) {
+    to_int<R>(h, p, u, 6, h->Uw, 6, 6, nullptr);
+    to_int<R>(h, p, v, 6, h->vA, 6, 6, nullptr);
+  }
   launch_dot<R>(h->q, (const R*)h->Uw, (const R*)h->vA, h->wdot, h->partials, h->bt, h->stream);
   launch_finalize(h->partials, h->bt, h->sc, nullptr, nullptr, 3, 0.0, h->stream);
   h->launches += 2;
@@ -773,15 +811,22 @@ int fw_dev(cmcg_handle* h, int periods, const double* const* j_re, const double*
   return check_err(h);
 }
 
-void free_all(cmcg_handle* h) {
+// Forgets the captured sweep graphs (their launches embed the stage arguments); the next
+// sweep of each kind is captured again.
+void drop_graphs(cmcg_handle* h) {
   for (auto& kv : h->graph_exec) cudaGraphExecDestroy(kv.second);
   h->graph_exec.clear();
+}
+
+void free_all(cmcg_handle* h) {
+  drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->cap_stream = nullptr;
   void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
                   h->Fre, h->Fim, h->Jre, h->Jim, h->Bre, h->Bim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
                   h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
-                  h->ext0, h->ext1, h->ext2, h->ext3, h->used, h->err};
+                  h->ext0, h->ext1, h->ext2, h->ext3, h->used, h->err, h->halo_dst, h->halo_src, h->g_in,
+                  h->g_out, h->inv_eps_g};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->sc_host) cudaFreeHost(h->sc_host);
@@ -872,6 +917,8 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
             P.imp.push_back(F);
           }
       e_of_i.insert(e_of_i.end(), L.ext_of_int.begin(), L.ext_of_int.end());
+      P.ext_of_int = L.ext_of_int;
+      P.int_of_ext = L.int_of_ext;
       for (int64_t t = 0; t < L.ntiles; ++t) tprob.push_back(p);
       for (int64_t k = 0; k < L.nt; ++k) inv_eps.push_back(1.0 / probs[p].eps[k]);
       h->nti += L.nti;
@@ -989,7 +1036,26 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
   return CMCG_OK;
 }
 
-bool single(const cmcg_handle* h) { return h && h->nprob == 1; }
+bool single(const cmcg_handle* h) { return h && (h->nprob == 1 || h->coupled); }
+
+// CMCG on a sharded handle: every part reads the global source and writes its owned results
+// into the global outputs (device pointers); the report is the parts' common one.
+int solve_sharded(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
+                  double* e_im, double* h_re, double* h_im, cmcg_info* info) {
+  if (!j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  const size_t n = size_t(h->nprob);
+  std::vector<const double*> jr(n, j_re), ji(n, j_im);
+  std::vector<double*> er(n, e_re), ei(n, e_im), hr(n, h_re), hi(n, h_im);
+  std::vector<cmcg_info> infos(n);
+  const int rc = h->prec == CMCG_FP32 ? solve_dev<float>(h, h->nprob, jr.data(), ji.data(), tol, max_iter, er.data(),
+                                                         ei.data(), hr.data(), hi.data(), infos.data())
+                                      : solve_dev<double>(h, h->nprob, jr.data(), ji.data(), tol, max_iter, er.data(),
+                                                          ei.data(), hr.data(), hi.data(), infos.data());
+  if (info) *info = infos[0];
+  return rc;
+}
+bool batch_ok(const cmcg_handle* h) { return h && !h->coupled; }
 
 }  // namespace
 
@@ -1067,6 +1133,92 @@ int cmcg_create_batch(int nprob, const cmcg_problem* probs, const cmcg_options* 
   return create_impl(nprob, probs, opt, out);
 }
 
+int cmcg_create_sharded(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
+                        const cmcg_options* opt_in, int nparts, const int32_t* part, cmcg_handle** out) {
+  if (!out) return CMCG_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!mesh || !eps || !mu || !part || nparts < 1) return CMCG_ERR_INVALID_ARG;
+  cmcg_options opt;
+  if (opt_in) opt = *opt_in;
+  else cmcg_default_options(&opt);
+  // The global problem fixes M (Eq. cfl over all tetrahedra); every part steps with it.
+  HostLayout G;
+  std::string why;
+  const size_t npt = static_cast<size_t>(nparts);
+  std::vector<ShardPlan> plans(npt);
+  std::vector<std::vector<int32_t>> tets(npt);
+  std::vector<std::vector<double>> peps(npt), pmu(npt);
+  std::vector<cmcg_mesh> meshes(npt);
+  std::vector<cmcg_problem> probs(npt);
+  try {
+    int rc = validate_and_layout(mesh, eps, mu, omega, &opt, &G, false, &why);
+    if (rc) return rc;
+    if (nparts > mesh->nt) return CMCG_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < mesh->nt; ++k)
+      if (part[k] < 0 || part[k] >= nparts) return CMCG_ERR_INVALID_ARG;
+    std::vector<int64_t> nb;
+    if (!match_faces(mesh, &nb)) return CMCG_ERR_NONCONFORMING_MESH;
+    for (int p = 0; p < nparts; ++p) {
+      if ((rc = shard_plan(mesh, nb, part, nparts, p, &plans[size_t(p)]))) return rc;
+      const ShardPlan& S = plans[size_t(p)];
+      if (S.n_owned == 0) return CMCG_ERR_INVALID_ARG;  // every part owns a tetrahedron
+      for (int32_t k : S.global_of_local) {
+        for (int v = 0; v < 4; ++v) tets[size_t(p)].push_back(mesh->tets[4 * int64_t(k) + v]);
+        peps[size_t(p)].push_back(eps[k]);
+        pmu[size_t(p)].push_back(mu[k]);
+      }
+      meshes[size_t(p)] = cmcg_mesh{mesh->nv, mesh->verts, int64_t(S.global_of_local.size()), tets[size_t(p)].data(),
+                                    S.local_tags.data()};
+      probs[size_t(p)] = cmcg_problem{&meshes[size_t(p)], peps[size_t(p)].data(), pmu[size_t(p)].data(), omega};
+    }
+  } catch (const std::bad_alloc&) {
+    return CMCG_ERR_OUT_OF_MEMORY;
+  }
+  opt.steps_per_period = G.steps;
+  cmcg_handle* h = nullptr;
+  int rc = create_impl(nparts, probs.data(), &opt, &h);
+  if (rc) return rc;
+  auto fail = [&](int code) {
+    cmcg_destroy(h);
+    return code;
+  };
+  h->coupled = true;
+  h->nt_global = mesh->nt;
+  h->bt.coupled = 1;
+  // Halo pairs (ghost <- owner) and the internal -> global maps.
+  std::vector<int64_t> hdst, hsrc;
+  std::vector<int32_t> gin(static_cast<size_t>(h->nti), -1), gout(static_cast<size_t>(h->nti), -1);
+  for (int p = 0; p < nparts; ++p) {
+    const ShardPlan& S = plans[size_t(p)];
+    const Prob& P = h->P[size_t(p)];
+    for (size_t g = 0; g < S.ghost_owner_part.size(); ++g) {
+      const Prob& Q = h->P[size_t(S.ghost_owner_part[g])];
+      hdst.push_back(P.tet0 + P.int_of_ext[size_t(S.n_owned) + g]);
+      hsrc.push_back(Q.tet0 + Q.int_of_ext[size_t(S.ghost_owner_local[g])]);
+    }
+    for (int64_t i = 0; i < P.nti; ++i) {
+      const int32_t e = P.ext_of_int[size_t(i)];
+      if (e < 0) continue;
+      gin[size_t(P.tet0 + i)] = S.global_of_local[size_t(e)];
+      if (e < S.n_owned) gout[size_t(P.tet0 + i)] = S.global_of_local[size_t(e)];
+    }
+  }
+  std::vector<double> ieg(static_cast<size_t>(mesh->nt));
+  for (int64_t k = 0; k < mesh->nt; ++k) ieg[size_t(k)] = 1.0 / eps[k];
+  size_t bytes = 0;
+  if ((rc = upload((void**)&h->halo_dst, hdst, &bytes)) || (rc = upload((void**)&h->halo_src, hsrc, &bytes)) ||
+      (rc = upload((void**)&h->g_in, gin, &bytes)) || (rc = upload((void**)&h->g_out, gout, &bytes)) ||
+      (rc = upload((void**)&h->inv_eps_g, ieg, &bytes)))
+    return fail(rc);
+  h->bytes += bytes;
+  h->nhalo = int64_t(hdst.size());
+  // ghosts do not count in the inner products (their owners do)
+  launch_zero_wdot(h->wdot, h->halo_dst, h->nhalo, h->stream);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess || cudaGetLastError() != cudaSuccess) return fail(CMCG_ERR_CUDA);
+  *out = h;
+  return CMCG_OK;
+}
+
 void cmcg_destroy(cmcg_handle* h) {
   if (!h) return;
   cudaSetDevice(h->device);
@@ -1082,11 +1234,12 @@ int cmcg_set_stream(cmcg_handle* h, void* stream) {
 
 int cmcg_get_sizes(const cmcg_handle* h, int64_t* nt, int* np, int* steps, double* dt, int64_t* field_len) {
   if (!h) return CMCG_ERR_INVALID_ARG;
-  if (nt) *nt = h->P[0].nt;
+  const int64_t n = h->coupled ? h->nt_global : h->P[0].nt;
+  if (nt) *nt = n;
   if (np) *np = h->np;
   if (steps) *steps = h->P[0].M;
   if (dt) *dt = h->P[0].dt;
-  if (field_len) *field_len = h->P[0].nt * 6 * h->np;
+  if (field_len) *field_len = n * 6 * h->np;
   return CMCG_OK;
 }
 
@@ -1106,7 +1259,7 @@ int cmcg_get_tuning(const cmcg_handle* h, int* variant, double* us_per_stage) {
   if (!h) return CMCG_ERR_INVALID_ARG;
   if (variant) *variant = h->form;
   if (us_per_stage)
-    for (int i = 0; i < 8; ++i) us_per_stage[i] = h->tune_us[i];
+    for (int i = 0; i < 10; ++i) us_per_stage[i] = h->tune_us[i];
   return CMCG_OK;
 }
 
@@ -1138,7 +1291,7 @@ int dgtd_apply(cmcg_handle* h, double t, const double* u, const double* j_re, co
                double* out) {
   if (!single(h) || !u || !out) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t n = size_t(h->nt_total) * 6 * h->np, nj = size_t(h->nt_total) * 3 * h->np;
+  const size_t n = size_t(ext_nt(h)) * 6 * h->np, nj = size_t(ext_nt(h)) * 3 * h->np;
   CK(cudaMemcpyAsync(h->ext0, u, n * 8, cudaMemcpyHostToDevice, h->stream));
   if (j_re) CK(cudaMemcpyAsync(h->ext2, j_re, nj * 8, cudaMemcpyHostToDevice, h->stream));
   if (j_re && j_im) CK(cudaMemcpyAsync(h->ext3, j_im, nj * 8, cudaMemcpyHostToDevice, h->stream));
@@ -1170,7 +1323,7 @@ int dgtd_period_forward(cmcg_handle* h, const double* u0, const double* j_re, co
                         double* filt_re, double* filt_im) {
   if (!single(h) || !u0) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t n = size_t(h->nt_total) * 6 * h->np, nj = size_t(h->nt_total) * 3 * h->np;
+  const size_t n = size_t(ext_nt(h)) * 6 * h->np, nj = size_t(ext_nt(h)) * 3 * h->np;
   // ext0: u0 / uT, ext1: filter re, ext2: filter im, ext3: j (re, then im)
   CK(cudaMemcpyAsync(h->ext0, u0, n * 8, cudaMemcpyHostToDevice, h->stream));
   const double* jr = nullptr;
@@ -1200,7 +1353,7 @@ int dgtd_period_forward(cmcg_handle* h, const double* u0, const double* j_re, co
 int dgtd_period_adjoint(cmcg_handle* h, const double* wT, double* w0) {
   if (!single(h) || !wT || !w0) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t n = size_t(h->nt_total) * 6 * h->np;
+  const size_t n = size_t(ext_nt(h)) * 6 * h->np;
   CK(cudaMemcpyAsync(h->ext0, wT, n * 8, cudaMemcpyHostToDevice, h->stream));
   int rc = DISPATCH(h, adjoint_dev<float>(h, h->ext0, h->ext0), adjoint_dev<double>(h, h->ext0, h->ext0));
   if (rc) return rc;
@@ -1212,7 +1365,7 @@ int dgtd_period_adjoint(cmcg_handle* h, const double* wT, double* w0) {
 int cmcg_inner(cmcg_handle* h, const double* u, const double* v, double* out) {
   if (!single(h) || !u || !v || !out) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
-  const size_t n = size_t(h->nt_total) * 6 * h->np;
+  const size_t n = size_t(ext_nt(h)) * 6 * h->np;
   CK(cudaMemcpyAsync(h->ext0, u, n * 8, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->ext1, v, n * 8, cudaMemcpyHostToDevice, h->stream));
   return DISPATCH(h, inner_dev<float>(h, h->ext0, h->ext1, out), inner_dev<double>(h, h->ext0, h->ext1, out));
@@ -1221,7 +1374,8 @@ int cmcg_inner(cmcg_handle* h, const double* u, const double* v, double* out) {
 int cmcg_solve_batch_device(cmcg_handle* h, const double* const* j_re, const double* const* j_im, double tol,
                             int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
                             double* const* h_im, cmcg_info* info) {
-  if (!h || !j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0) return CMCG_ERR_INVALID_ARG;
+  if (!batch_ok(h) || !j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0)
+    return CMCG_ERR_INVALID_ARG;
   for (int p = 0; p < h->nprob; ++p)
     if (!j_re[p] || !e_re[p] || !e_im[p] || !h_re[p] || !h_im[p]) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
@@ -1279,7 +1433,7 @@ int copy_host_outputs(cmcg_handle* h, int n, const HostIO& io, double* const* e_
 
 bool host_args_ok(const cmcg_handle* h, int n, const double* const* j_re, double* const* e_re, double* const* e_im,
                   double* const* h_re, double* const* h_im) {
-  if (!h || n < 1 || n > h->nprob || !j_re || !e_re || !e_im || !h_re || !h_im) return false;
+  if (!batch_ok(h) || n < 1 || n > h->nprob || !j_re || !e_re || !e_im || !h_re || !h_im) return false;
   for (int p = 0; p < n; ++p)
     if (!j_re[p] || !e_re[p] || !e_im[p] || !h_re[p] || !h_im[p]) return false;
   return true;
@@ -1308,7 +1462,7 @@ int cmcg_solve_batch_n(cmcg_handle* h, int n, const double* const* j_re, const d
 }
 
 int cmcg_set_boundary_data(cmcg_handle* h, int problem, const double* g_re, const double* g_im) {
-  if (!h || problem < 0 || problem >= h->nprob) return CMCG_ERR_INVALID_ARG;
+  if (!batch_ok(h) || problem < 0 || problem >= h->nprob) return CMCG_ERR_INVALID_ARG;
   if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
   Prob& P = h->P[problem];
   const int np = h->np, nfp = nfp_of(h->q);
@@ -1415,6 +1569,45 @@ int cmcg_set_boundary_data(cmcg_handle* h, int problem, const double* g_re, cons
   return CMCG_OK;
 }
 
+int cmcg_set_conductivity(cmcg_handle* h, int problem, const double* sigma) {
+  if (!batch_ok(h) || problem < 0 || problem >= h->nprob) return CMCG_ERR_INVALID_ARG;
+  Prob& P = h->P[problem];
+  const int s = h->s;
+  // Real-axis stability of the explicit step: the damping -sigma/eps alone needs
+  // dt sigma / eps within the RK interval (2 for RK2, about 2.78 for RK4); 2 is required.
+  if (sigma) {
+    std::vector<double> ie(static_cast<size_t>(P.nt));
+    if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+    CK(cudaMemcpy(ie.data(), h->inv_eps + P.ext0, ie.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < P.nt; ++k) {
+      if (!(sigma[k] >= 0) || !std::isfinite(sigma[k])) return CMCG_ERR_INVALID_ARG;
+      if (P.dt * sigma[k] * ie[size_t(k)] > 2.0) return CMCG_ERR_INVALID_ARG;
+    }
+  } else if (cudaSetDevice(h->device) != cudaSuccess) {
+    return CMCG_ERR_CUDA;
+  }
+  (void)s;
+  double* dsig = h->ext0;  // staging: nt_total * 6 Np doubles >= nt
+  if (sigma) {
+    CK(cudaMemcpyAsync(dsig, sigma, size_t(P.nt) * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  } else {
+    CK(cudaMemsetAsync(dsig, 0, size_t(P.nt) * sizeof(double), h->stream));
+  }
+  void* gv = static_cast<char*>(h->gvol) + size_t(P.tile0) * GV * TILE * h->rsize;
+  if (h->prec == CMCG_FP32)
+    launch_set_gvol_item<float>((float*)gv, 11, dsig, h->inv_eps + P.ext0, h->e_of_i + P.tet0, P.nti, h->stream);
+  else
+    launch_set_gvol_item<double>((double*)gv, 11, dsig, h->inv_eps + P.ext0, h->e_of_i + P.tet0, P.nti, h->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  P.has_sigma = sigma != nullptr;
+  bool any = false;
+  for (const Prob& Q : h->P) any = any || Q.has_sigma;
+  if (any != h->has_sigma) drop_graphs(h);
+  h->has_sigma = any;
+  return CMCG_OK;
+}
+
 int cmcg_fw_solve_batch(cmcg_handle* h, int periods, const double* const* j_re, const double* const* j_im,
                         double* const* e_re, double* const* e_im, double* const* h_re, double* const* h_im) {
   if (!host_args_ok(h, h ? h->nprob : 0, j_re, e_re, e_im, h_re, h_im) || periods < 0) return CMCG_ERR_INVALID_ARG;
@@ -1449,13 +1642,32 @@ int64_t cmcg_device_bytes(const cmcg_handle* h) { return h ? int64_t(h->bytes) :
 int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
                       double* e_im, double* h_re, double* h_im, cmcg_info* info) {
   if (!single(h)) return CMCG_ERR_INVALID_ARG;
-  return cmcg_solve_batch_device(h, &j_re, &j_im, tol, max_iter, &e_re, &e_im, &h_re, &h_im, info);
+  if (!h->coupled) return cmcg_solve_batch_device(h, &j_re, &j_im, tol, max_iter, &e_re, &e_im, &h_re, &h_im, info);
+  return solve_sharded(h, j_re, j_im, tol, max_iter, e_re, e_im, h_re, h_im, info);
 }
 
 int cmcg_solve(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
                double* e_im, double* h_re, double* h_im, cmcg_info* info) {
   if (!single(h)) return CMCG_ERR_INVALID_ARG;
-  return cmcg_solve_batch(h, &j_re, &j_im, tol, max_iter, &e_re, &e_im, &h_re, &h_im, info);
+  if (!h->coupled) return cmcg_solve_batch(h, &j_re, &j_im, tol, max_iter, &e_re, &e_im, &h_re, &h_im, info);
+  if (!j_re || !e_re || !e_im || !h_re || !h_im || !(tol >= 0) || max_iter < 0) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  // global source into ext3 (re, then im), results into ext0 (e) and ext1 (h)
+  const size_t nj = size_t(h->nt_global) * 3 * h->np;
+  CK(cudaMemcpyAsync(h->ext3, j_re, nj * 8, cudaMemcpyHostToDevice, h->stream));
+  const double* ji = nullptr;
+  if (j_im) {
+    CK(cudaMemcpyAsync(h->ext3 + nj, j_im, nj * 8, cudaMemcpyHostToDevice, h->stream));
+    ji = h->ext3 + nj;
+  }
+  int rc = solve_sharded(h, h->ext3, ji, tol, max_iter, h->ext0, h->ext0 + nj, h->ext1, h->ext1 + nj, info);
+  if (rc < 0) return rc;
+  CK(cudaMemcpyAsync(e_re, h->ext0, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(e_im, h->ext0 + nj, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h_re, h->ext1, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h_im, h->ext1 + nj, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return rc;
 }
 
 }  // extern "C"

@@ -79,11 +79,29 @@ struct HostLayout {
   double dt = 0, T = 0, rho_min = 0;
   int ngroups = 0;
 };
-constexpr int GV = 12;  // G (9, d r_b / d x_a at [b*3+a]), 1/eps, 1/mu, pad
+constexpr int GV = 12;  // G (9, d r_b / d x_a at [b*3+a]), 1/eps, 1/mu, sigma/eps (0 unless set)
 constexpr int GF = 8;   // nx, ny, nz, bH, aH, -bE, aE, pad  (see setup.cpp)
 
 int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
                         const cmcg_options* opt, HostLayout* out, bool build_layout, std::string* why);
+// Face neighbours by sorted vertex triples: (*nb)[4 k + f] = 4 k' + f' or -1 (vertex indices must
+// be in range); false if a face is shared by more than two tetrahedra.
+bool match_faces(const cmcg_mesh* mesh, std::vector<int64_t>* nb);
+
+// Element partition of a mesh (host only).  Part p's local mesh lists its owned tetrahedra (in
+// increasing global order) followed by its ghosts: the tetrahedra of other parts that share a
+// face with an owned one (increasing global order).  A ghost face whose neighbour is not in the
+// local mesh is tagged PEC there (ghost values are replaced after every stage, so those faces
+// never reach an owned result).
+struct ShardPlan {
+  int64_t n_owned = 0;
+  std::vector<int32_t> global_of_local;    // owned, then ghosts
+  std::vector<int32_t> ghost_owner_part;   // per ghost
+  std::vector<int32_t> ghost_owner_local;  // per ghost: its index in the owner's local numbering
+  std::vector<uint8_t> local_tags;         // [n_local][4]
+};
+int shard_plan(const cmcg_mesh* mesh, const std::vector<int64_t>& nb, const int32_t* part, int nparts, int p,
+               ShardPlan* out);
 
 // Neighbour code: >= 0: (internal neighbour << 5) | (neighbour face << 3) | perm.
 constexpr int32_t NBR_PEC = -1;
@@ -91,7 +109,8 @@ constexpr int32_t NBR_IMP = -2;
 
 // Per-problem coefficients of one stage launch (a handle holds a batch of
 // problems that advance in lockstep; each reads its own entry).
-//   Phi   = src + B_sigma(vin),  src = s_cos * (jre + bre) - s_sin * (jim + bim)   (B_sigma = Sigma B Sigma when sH = -1)
+//   Phi   = src + B_sigma(vin),  src = s_cos * (jre + bre) - s_sin * (jim + bim)   (B_sigma = Sigma B Sigma when sH = -1;
+//           B carries -(sigma/eps) E on the E rows when a.sigma is set)
 //   out   = base + c_out Phi        (skipped if out == nullptr)
 //   acc_o = acc_i + c_acc Phi       (skipped if acc_o == nullptr)
 //   F    += fa vin + fb Phi         (complex weights; skipped if fre == nullptr)
@@ -125,18 +144,20 @@ struct StageArgs {
   const int32_t* nbr;
   int64_t nti;
   int32_t* err;  // device status word: a stage kernel whose bounded wait ran out ORs in 1 (null: not recorded)
+  int32_t sigma;  // nonzero: some tetrahedron has a conductivity (sigma/eps in gvol item 11)
 };
 
 // Kernel launchers, one translation unit per order.
 // form: stage-kernel form.  FP32: 0, 1, 2 = two threads per tetrahedron with at
 // least 1, 3, 4 resident 128-thread blocks per SM; 3, 4, 5 = four threads per
-// tetrahedron with at least 4, 5, 6; 6 = tensor-core contractions (tcgen05,
-// 3xTF32) with two threads per tetrahedron.  FP64: 0 = two threads per
+// tetrahedron with at least 4, 5, 6; 6, 7 = tensor-core contractions (tcgen05,
+// 3xTF32) with two / four threads per tetrahedron.  FP64: 0 = two threads per
 // tetrahedron, 1, 2 = four threads per tetrahedron with at least 2, 3 blocks.
 // pdl: launch with programmatic stream serialisation (the stage overlaps the
 // previous stage's tail).
-constexpr int STAGE_FORMS_F32 = 7;
+constexpr int STAGE_FORMS_F32 = 8;
 constexpr int STAGE_FORM_TC = 6;
+constexpr int STAGE_FORM_TC4 = 7;
 constexpr int STAGE_FORMS_F64 = 3;
 template <int Q, typename R>
 void launch_stage(const StageArgs<R>& a, cudaStream_t s, int form, bool pdl);
@@ -160,6 +181,8 @@ struct BlockTable {
   const int32_t* pb0;
   int nblk;
   int nprob;
+  int coupled;  // nonzero: the problems are the parts of one sharded problem; every problem's
+                // scalars are the sums over all blocks (the all-reduce of a sharded CG)
 };
 constexpr int DOT_THREADS = 128;
 
@@ -192,6 +215,17 @@ void launch_dot(int q, const R* X, const R* Y, const double* wdot, double* parti
 template <typename R>
 void launch_scatter_rows(R* dst_re, R* dst_im, const double* src_re, const double* src_im, const int64_t* tet,
                          int64_t count, int np, cudaStream_t s);
+// Halo exchange of a sharded handle: the 6 Np values of internal tetrahedron src[i] are copied
+// to internal tetrahedron dst[i] of the same field vector (a ghost receives its owner's values).
+template <typename R>
+void launch_halo(R* v, const int64_t* dst, const int64_t* src, int64_t n, int np, cudaStream_t s);
+// wdot = 0 for the listed internal tetrahedra (ghosts do not count in the inner products).
+void launch_zero_wdot(double* wdot, const int64_t* tets, int64_t n, cudaStream_t s);
+// gvol item `item` of a problem's internal tetrahedra [0, nti) = val[e] * scale[e], e = e_of_i[i]
+// (device arrays in the problem's external order; padding gets 0).
+template <typename R>
+void launch_set_gvol_item(R* gvol, int item, const double* val, const double* scale, const int32_t* e_of_i,
+                          int64_t nti, cudaStream_t s);
 // D = R + beta_p D and Uw = D on the tiles of active problems.
 template <typename R>
 void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob, const int32_t* pactive,

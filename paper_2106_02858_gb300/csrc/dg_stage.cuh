@@ -259,6 +259,14 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
     }
   }
 
+  if (half && a.sigma) {  // conductivity: Phi_E -= (sigma / eps) E (E is not flipped by Sigma)
+    const R so = a.gvol[(tile * GV + 11) * TILE + lane];
+    const R* ev = a.vin + tile * VS + lane;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int n = 0; n < NP; ++n) phi[c][n] -= so * ev[(c * NP + n) * TILE];
+  }
   if (half && a.jre) {  // source on the E rows
     const int64_t joff = tile * (3 * NP * TILE) + lane;
 #pragma unroll
@@ -515,6 +523,14 @@ __device__ __forceinline__ void quad_stage(const StageArgs<R>& a) {
     }
   }
 
+  if (half && a.sigma) {  // conductivity: Phi_E -= (sigma / eps) E on this half's nodes
+    const R so = a.gvol[(tile * GV + 11) * TILE + lane];
+    const R* ev = a.vin + tile * VS + lane;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int ii = 0; ii < NH; ++ii) phi[c][ii] -= so * ev[(c * NP + I0 + ii) * TILE];
+  }
   if (half && a.jre) {  // source on the E rows
     const int64_t joff = tile * (3 * NP * TILE) + lane;
 #pragma unroll
@@ -615,6 +631,10 @@ void launch_stage<CMCG_Q, float>(const StageArgs<float>& a, cudaStream_t s, int 
       launch_k(dg_stage_tc<TC_MINB>, unsigned((a.nti + TC_TETS - 1) / TC_TETS), TC_THREADS,
                tc_smem(a.acc_out != nullptr), s, pdl, a);
       break;
+    case STAGE_FORM_TC4:
+      launch_k(dg_stage_tc4<TC_MINB>, unsigned((a.nti + TC_TETS - 1) / TC_TETS), T4_THREADS,
+               tc4_smem(a.acc_out != nullptr), s, pdl, a);
+      break;
     default: launch_k(dg_stage_kernel<float, 1>, blocks, STAGE_THREADS, sm, s, pdl, a); break;
   }
 }
@@ -643,6 +663,7 @@ void upload_constants<CMCG_Q>(const RefMats& rm) {
   cudaFuncSetAttribute(dg_stage_quad<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<double>()));
   cudaFuncSetAttribute(dg_stage_quad<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<double>()));
   cudaFuncSetAttribute(dg_stage_tc<TC_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc_smem(true)));
+  cudaFuncSetAttribute(dg_stage_tc4<TC_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc4_smem(true)));
   tc_upload_reference(rm);
   const int np = rm.np, nfp = rm.nfp;
   std::vector<double> D(3 * np * np);

@@ -44,6 +44,31 @@ int fail(std::string* why, const std::string& msg, int code) {
 
 }  // namespace
 
+bool match_faces(const cmcg_mesh* mesh, std::vector<int64_t>* nb_out) {
+  const int64_t nt = mesh->nt;
+  const int32_t* T = mesh->tets;
+  std::vector<int64_t>& nb = *nb_out;
+  nb.assign(size_t(4 * nt), -1);
+  std::unordered_map<FaceKey, int64_t, FaceKeyHash> map;
+  map.reserve(size_t(4 * nt));
+  for (int64_t k = 0; k < nt; ++k)
+    for (int f = 0; f < 4; ++f) {
+      int32_t g[3] = {T[4 * k + FACE_VERTS[f][0]], T[4 * k + FACE_VERTS[f][1]], T[4 * k + FACE_VERTS[f][2]]};
+      std::sort(g, g + 3);
+      FaceKey key{g[0], g[1], g[2]};
+      auto it = map.find(key);
+      if (it == map.end()) {
+        map.emplace(key, 4 * k + f);
+      } else {
+        if (it->second < 0) return false;
+        nb[4 * k + f] = it->second;
+        nb[it->second] = 4 * k + f;
+        it->second = -1;
+      }
+    }
+  return true;
+}
+
 int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* mu, double omega,
                         const cmcg_options* opt, HostLayout* out, bool build_layout, std::string* why) {
   if (!mesh || !eps || !mu || !opt) return fail(why, "null argument", CMCG_ERR_INVALID_ARG);
@@ -137,26 +162,8 @@ int validate_and_layout(const cmcg_mesh* mesh, const double* eps, const double* 
   }
 
   // --- face matching -------------------------------------------------------------------------
-  std::vector<int64_t> nb(4 * nt, -1);  // neighbour (tet*4 + face)
-  {
-    std::unordered_map<FaceKey, int64_t, FaceKeyHash> map;
-    map.reserve(size_t(4 * nt));
-    for (int64_t k = 0; k < nt; ++k)
-      for (int f = 0; f < 4; ++f) {
-        int32_t g[3] = {T[4 * k + FACE_VERTS[f][0]], T[4 * k + FACE_VERTS[f][1]], T[4 * k + FACE_VERTS[f][2]]};
-        std::sort(g, g + 3);
-        FaceKey key{g[0], g[1], g[2]};
-        auto it = map.find(key);
-        if (it == map.end()) {
-          map.emplace(key, 4 * k + f);
-        } else {
-          if (it->second < 0) return fail(why, "a face is shared by more than two tetrahedra", CMCG_ERR_NONCONFORMING_MESH);
-          nb[4 * k + f] = it->second;
-          nb[it->second] = 4 * k + f;
-          it->second = -1;
-        }
-      }
-  }
+  std::vector<int64_t> nb;  // neighbour (tet*4 + face)
+  if (!match_faces(mesh, &nb)) return fail(why, "a face is shared by more than two tetrahedra", CMCG_ERR_NONCONFORMING_MESH);
   for (int64_t kf = 0; kf < 4 * nt; ++kf) {
     uint8_t t = mesh->face_tags[kf];
     if (nb[kf] >= 0 && t != CMCG_TAG_INTERIOR)

@@ -230,6 +230,34 @@ __global__ void scatter_rows_kernel(R* dst_re, R* dst_im, const double* src_re, 
   }
 }
 
+template <typename R>
+__global__ void halo_kernel(R* v, const int64_t* dst, const int64_t* src, int64_t n, int rows) {
+  const int64_t total = n * rows;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / rows, k = i % rows, d = dst[e], s = src[e];
+    v[(d >> 5) * rows * TILE + k * TILE + (d & 31)] = v[(s >> 5) * rows * TILE + k * TILE + (s & 31)];
+  }
+}
+
+__global__ void zero_wdot_kernel(double* wdot, const int64_t* tets, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = tets[i];
+    wdot[((t >> 5) * 2 + 0) * TILE + (t & 31)] = 0.0;
+    wdot[((t >> 5) * 2 + 1) * TILE + (t & 31)] = 0.0;
+  }
+}
+
+// gvol item `item` of internal tetrahedra [0, nti) of one problem: val[e] * scale[e] for the
+// external tetrahedron e = e_of_i[i] (0 on padding).
+template <typename R>
+__global__ void set_gvol_item_kernel(R* gvol, int item, const double* val, const double* scale,
+                                     const int32_t* e_of_i, int64_t nti) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nti; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t e = e_of_i[i];
+    gvol[((i >> 5) * GV + item) * TILE + (i & 31)] = e >= 0 ? R(val[e] * scale[e]) : R(0);
+  }
+}
+
 // D = R + beta_p D; Uw = D (active problems only).
 template <typename R>
 __global__ void cg_direction_kernel(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob,
@@ -247,7 +275,7 @@ __global__ void finalize_kernel(const double* partials, const BlockTable bt, Sca
                                 const int32_t* used, int which, double tol) {
   __shared__ double sh[256];
   const int p = blockIdx.x;
-  const int b0 = bt.pb0[p], b1 = bt.pb0[p + 1];
+  const int b0 = bt.coupled ? 0 : bt.pb0[p], b1 = bt.coupled ? bt.nblk : bt.pb0[p + 1];
   auto reduce = [&](const double* part) {
     double s = 0;
     for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) s += part[i];
@@ -376,6 +404,21 @@ void launch_scatter_rows(R* dst_re, R* dst_im, const double* src_re, const doubl
                                                                          6 * np);
 }
 template <typename R>
+void launch_halo(R* v, const int64_t* dst, const int64_t* src, int64_t n, int np, cudaStream_t s) {
+  if (n <= 0) return;
+  halo_kernel<R><<<grid_for(n * 6 * np, 256), 256, 0, s>>>(v, dst, src, n, 6 * np);
+}
+void launch_zero_wdot(double* wdot, const int64_t* tets, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  zero_wdot_kernel<<<grid_for(n, 256), 256, 0, s>>>(wdot, tets, n);
+}
+template <typename R>
+void launch_set_gvol_item(R* gvol, int item, const double* val, const double* scale, const int32_t* e_of_i,
+                          int64_t nti, cudaStream_t s) {
+  if (nti <= 0) return;
+  set_gvol_item_kernel<R><<<grid_for(nti, 256), 256, 0, s>>>(gvol, item, val, scale, e_of_i, nti);
+}
+template <typename R>
 void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int32_t* tprob, const int32_t* pactive,
                          int64_t n, int np, cudaStream_t s) {
   cg_direction_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(D, Uw, Rv, sc, tprob, pactive, n, int64_t(6) * np * TILE);
@@ -398,6 +441,9 @@ void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, 
   template void launch_dot<R>(int, const R*, const R*, const double*, double*, const BlockTable&, cudaStream_t);      \
   template void launch_scatter_rows<R>(R*, R*, const double*, const double*, const int64_t*, int64_t, int,        \
                                        cudaStream_t);                                                              \
+  template void launch_set_gvol_item<R>(R*, int, const double*, const double*, const int32_t*, int64_t,             \
+                                        cudaStream_t);                                                             \
+  template void launch_halo<R>(R*, const int64_t*, const int64_t*, int64_t, int, cudaStream_t);                        \
   template void launch_cg_direction<R>(R*, R*, const R*, const Scalars*, const int32_t*, const int32_t*, int64_t,     \
                                        int, cudaStream_t);
 CMCG_INST(float)

@@ -242,18 +242,32 @@ def uneven_batch(seed: int = 0, count: int = 64, n_range=(6, 20), tol: float = 1
         n = int(rng.integers(n_range[0], n_range[1] + 1))
         q = int(rng.integers(1, 4))
         omega = float(rng.choice([2 * np.pi, 4 * np.pi, 8 * np.pi]))
-        blocks = rng.uniform(1.0, 4.0, 8)
-        centre = rng.uniform(0.2, 0.8, 3)
-        pol = unit_vector(rng)
-
-        def eps_fn(cen, blocks=blocks):
-            idx = (cen[:, 0] >= 0.5).astype(int) + 2 * (cen[:, 1] >= 0.5) + 4 * (cen[:, 2] >= 0.5)
-            return blocks[idx]
-
-        prob = cube_problem(n, q, omega, centre, pol, 0.1, tol=tol, eps_fn=eps_fn, name=f"uneven{p}_n{n}_P{q}")
-        prob.meta.update({"blocks": blocks.tolist()})
-        out.append(prob)
+        out.append(block_eps_problem(n, q, omega, rng, tol=tol, name=f"uneven{p}_n{n}_P{q}"))
     return out
+
+
+def block_eps_problem(n: int, q: int, omega: float, rng: np.random.Generator, tol: float = 1e-5,
+                      name: str = "blocks") -> Problem:
+    """One problem of the uneven batch: the n^3 Kuhn cube at order q and frequency omega, eps
+    constant on the 2x2x2 block partition with values drawn U[1,4] from ``rng``, impedance outer
+    boundary, one Gaussian source (width 0.1) at a drawn centre with a drawn unit polarisation."""
+    blocks = rng.uniform(1.0, 4.0, 8)
+    centre = rng.uniform(0.2, 0.8, 3)
+    pol = unit_vector(rng)
+
+    def eps_fn(cen, blocks=blocks):
+        idx = (cen[:, 0] >= 0.5).astype(int) + 2 * (cen[:, 1] >= 0.5) + 4 * (cen[:, 2] >= 0.5)
+        return blocks[idx]
+
+    prob = cube_problem(n, q, omega, centre, pol, 0.1, tol=tol, eps_fn=eps_fn, name=name)
+    prob.meta.update({"blocks": blocks.tolist()})
+    return prob
+
+
+def block_eps_subset(shapes, seed: int = 1, tol: float = 1e-5) -> List[Problem]:
+    """Problems of the uneven batch's recipe at chosen (n, q, omega) shapes, drawn from one seed."""
+    rng = np.random.default_rng(seed)
+    return [block_eps_problem(n, q, w, rng, tol=tol, name=f"blocks_n{n}_P{q}") for n, q, w in shapes]
 
 
 @dataclass

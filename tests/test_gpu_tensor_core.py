@@ -1,4 +1,5 @@
-"""The tensor-core stage form (stage_variant 7) against the FP64 oracle (GPU).
+"""The tensor-core stage forms (stage_variant 7: two threads per tetrahedron, 8: four) against
+the FP64 oracle (GPU).
 
 The volume derivatives D_b F and the lift LIFT . f of the DG operator (Section
 5.2.2, Eq. DG_semidiscrete / Eq. ode_system) run as tcgen05 MMAs with three
@@ -23,7 +24,7 @@ from paper_2106_02858_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TC = 7  # stage_variant of the tensor-core form
+TC_FORMS = [7, 8]  # stage_variant of the tensor-core forms
 
 
 @pytest.fixture(scope="module")
@@ -81,8 +82,9 @@ CASES = [("single", 1), ("single", 3), ("cube3", 1), ("cube3", 2), ("cube3", 3),
          ("scatterer8", 2), ("scatterer8", 3), ("distorted", 2), ("distorted", 3), ("cube4", 3)]
 
 
+@pytest.mark.parametrize("TC", TC_FORMS)
 @pytest.mark.parametrize("kind,q", CASES)
-def test_tensor_core_operator_matches_oracle(lib, kind, q):
+def test_tensor_core_operator_matches_oracle(lib, kind, q, TC):
     from oracle.dg import Phi, apply_B
     p = _problem(kind, q)
     g = _geo(p)
@@ -97,7 +99,8 @@ def test_tensor_core_operator_matches_oracle(lib, kind, q):
 
 @pytest.mark.parametrize("kind,q", [("single", 2), ("cube3", 1), ("cube3", 3), ("scatterer8", 2),
                                     ("distorted", 3), ("cube4", 3)])
-def test_tensor_core_sweeps_match_oracle(lib, kind, q):
+@pytest.mark.parametrize("TC", TC_FORMS)
+def test_tensor_core_sweeps_match_oracle(lib, kind, q, TC):
     from oracle.timestep import Stepper
     from oracle.filtering import filtered_sweep
     p = _problem(kind, q)
@@ -114,7 +117,8 @@ def test_tensor_core_sweeps_match_oracle(lib, kind, q):
     h.close()
 
 
-def test_tensor_core_full_size_scatterer_operator(lib):
+@pytest.mark.parametrize("TC", TC_FORMS)
+def test_tensor_core_full_size_scatterer_operator(lib, TC):
     """The 81,648-tet P2 scatterer: one operator application of the tensor-core form vs the oracle."""
     from oracle.dg import Phi
     p = I.scatterer_sphere()
@@ -125,7 +129,8 @@ def test_tensor_core_full_size_scatterer_operator(lib):
     h.close()
 
 
-def test_tensor_core_cmcg_converged_matches_oracle(lib):
+@pytest.mark.parametrize("TC", TC_FORMS)
+def test_tensor_core_cmcg_converged_matches_oracle(lib, TC):
     from oracle import cmcg as ocmcg
     from oracle.timestep import Stepper
     p = _problem("cube3", 3)
@@ -138,7 +143,8 @@ def test_tensor_core_cmcg_converged_matches_oracle(lib):
     assert _rel(np.concatenate([e, hh], axis=1), ref.filtered, g) < 1e-4
 
 
-def test_tensor_core_batch_alone_vs_in_the_mix(lib):
+@pytest.mark.parametrize("TC", TC_FORMS)
+def test_tensor_core_batch_alone_vs_in_the_mix(lib, TC):
     """Problems of 162 and 48 tetrahedra (ragged tiles) share CTAs in one handle: each problem's
     result equals its solve alone with the same form (the rows of an MMA are independent)."""
     rng = np.random.default_rng(3)
