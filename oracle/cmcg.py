@@ -60,8 +60,19 @@ def functional(st: Stepper, U0, G) -> float:
 
 def solve(st: Stepper, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 500, track_functional: bool = False,
           U0: Optional[np.ndarray] = None) -> CMCGResult:
-    geo = st.geo
     G, Gstar = initialise(st, j_re, j_im)
+    U, it, converged, res, funcs, periods = iterate(st, G, Gstar, tol, max_iter, track_functional, U0)
+    F = filtered_sweep(st, U, j_re, j_im)
+    periods += 1
+    return CMCGResult(U0=U, filtered=F, iters=it, converged=converged, residuals=res, functionals=funcs,
+                      periods=periods)
+
+
+def iterate(st: Stepper, G, Gstar, tol: float, max_iter: int, track_functional: bool = False,
+            U0: Optional[np.ndarray] = None):
+    """Algorithm cmcg in residual form from the data G, G* of Algorithm init.  Returns
+    (U0, iterations, converged, relative residuals, functionals, periods simulated so far)."""
+    geo = st.geo
     periods = 2
     if U0 is None:
         U = np.zeros_like(Gstar)
@@ -99,7 +110,4 @@ def solve(st: Stepper, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 500, 
             funcs.append(functional(st, U, G))
     if not converged and np.sqrt(rr) <= tol * r0:
         converged = True
-    F = filtered_sweep(st, U, j_re, j_im)
-    periods += 1
-    return CMCGResult(U0=U, filtered=F, iters=it, converged=converged, residuals=res, functionals=funcs,
-                      periods=periods)
+    return U, it, converged, res, funcs, periods
