@@ -313,6 +313,22 @@ int dgtd_period_adjoint_device(cmcg_handle* h, const double* wT, double* w0);
 int cmcg_solve(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
                double* e_im, double* h_re, double* h_im, cmcg_info* info);
 
+/* Several frequencies in one solve (the Conclusion, Section 7: CMCG can compute the
+ * solutions of several frequencies "in one shot").  The handle's omega is the base
+ * frequency w0 (its period T0 = 2 pi / w0 and M as for a single solve); harmonic h
+ * has the frequency harmonics[h] w0 (an integer >= 1) and the current density
+ * j_re[h] + i j_im[h].  CMCG runs once on the period T0 with the summed source
+ * Re(sum_h J_h e^{i harmonics[h] w0 t}); then one filtered sweep from its U0 per
+ * harmonic, with the filter of Eq. filter at that harmonic's frequency over T0,
+ * writes e_re[h], e_im[h], h_re[h], h_im[h]: the time-harmonic field of frequency
+ * harmonics[h] w0.  Cost: one CMCG solve plus nharm - 1 sweeps.  nharm in 1..64;
+ * arrays of nharm host pointers to double[nt][3][Np] (j_im may be NULL, or any
+ * j_im[h]); single-problem handles only (not batch or sharded).  info: the one
+ * CG's report (periods include the extra sweeps). */
+int cmcg_solve_multifreq(cmcg_handle* h, int nharm, const int* harmonics, const double* const* j_re,
+                         const double* const* j_im, double tol, int max_iter, double* const* e_re,
+                         double* const* e_im, double* const* h_re, double* const* h_im, cmcg_info* info);
+
 /* (u, v)_{eps,mu} = sum_K int_K eps E_u . E_v + mu H_u . H_v (Eq. innerproduct),
  * i.e. V^T M U with the block-diagonal DG mass matrix, evaluated on the device
  * in FP64 (the fields are first rounded to the handle's precision).  u, v:

@@ -132,6 +132,9 @@ def _load() -> C.CDLL:
         "cmcg_profile_enable": (C.c_int, [_vp, C.c_int]),
         "cmcg_measure_peaks": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "cmcg_partition_slabs": (C.c_int, [C.POINTER(cmcg_mesh), C.c_int, C.c_int, C.POINTER(C.c_int32)]),
+        "cmcg_solve_multifreq": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_dp), C.POINTER(_dp),
+                                           C.c_double, C.c_int, C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp),
+                                           C.POINTER(_dp), C.POINTER(cmcg_info)]),
         "cmcg_shard_plan": (C.c_int, [C.POINTER(cmcg_mesh), C.POINTER(C.c_int32), C.c_int, C.c_int,
                                       C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                       C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_uint8)]),
@@ -157,7 +160,7 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_device_bytes", "cmcg_fw_solve", "cmcg_fw_solve_batch", "cmcg_set_boundary_data", "cmcg_server_default_options", "cmcg_server_create", "cmcg_server_add_model",
             "cmcg_server_submit", "cmcg_server_poll", "cmcg_server_stats", "cmcg_server_destroy",
             "cmcg_measure_peaks", "cmcg_set_conductivity", "cmcg_partition_slabs", "cmcg_shard_plan",
-            "cmcg_create_sharded")
+            "cmcg_create_sharded", "cmcg_solve_multifreq")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
 
@@ -289,6 +292,23 @@ def cmcg_create(mesh: MeshArrays, eps, mu, omega: float, opt: cmcg_options) -> H
     _check(_lib.cmcg_get_sizes(out, C.byref(nt), C.byref(np_), C.byref(steps), C.byref(dt), C.byref(fl)),
            "cmcg_get_sizes")
     return Handle(out.value, nt.value, np_.value, steps.value, dt.value)
+
+
+def cmcg_solve_multifreq(h: Handle, harmonics, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 1000):
+    """Several harmonics k * omega of the handle's base frequency in one CMCG solve: lists of
+    (nt, 3, Np) sources per harmonic; returns ([e], [h]) complex per harmonic and the report."""
+    K = len(harmonics)
+    jr = [_field(h, j_re[k], 3, "j_re") for k in range(K)]
+    ji = [None if (j_im is None or j_im[k] is None) else _field(h, j_im[k], 3, "j_im") for k in range(K)]
+    outs = [[np.empty((h.nt, 3, h.np)) for _ in range(K)] for _ in range(4)]
+    P = C.POINTER(C.c_double)
+    arr = lambda xs: (P * K)(*[_ptr(x) if x is not None else P() for x in xs])
+    harm = (C.c_int * K)(*[int(k) for k in harmonics])
+    info = cmcg_info()
+    rc = _lib.cmcg_solve_multifreq(h.ptr, K, harm, arr(jr), arr(ji), float(tol), int(max_iter), arr(outs[0]),
+                                   arr(outs[1]), arr(outs[2]), arr(outs[3]), C.byref(info))
+    _check(rc, "cmcg_solve_multifreq", allow_not_converged=True)
+    return ([outs[0][k] + 1j * outs[1][k] for k in range(K)], [outs[2][k] + 1j * outs[3][k] for k in range(K)], info)
 
 
 def cmcg_partition_slabs(mesh: MeshArrays, nparts: int, axis: int = 2) -> np.ndarray:

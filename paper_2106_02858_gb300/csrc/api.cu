@@ -114,6 +114,13 @@ struct cmcg_handle {
   int64_t *halo_dst = nullptr, *halo_src = nullptr;  // internal tetrahedra: ghost <- owner
   int32_t *g_in = nullptr, *g_out = nullptr;          // internal -> global tetrahedron (g_out: owned only)
   double* inv_eps_g = nullptr;                        // 1 / eps by global tetrahedron
+  // Several harmonics in one solve (cmcg_solve_multifreq): while mf_nharm > 0 the source sweeps
+  // read mf_nharm sources from Jm_re / Jm_im (njvec values apart) with the per-launch harmonic
+  // coefficients mf_hcs, and filtered sweeps use the filter table mf_tab of the harmonic being read.
+  int mf_nharm = 0, mf_cap = 0;
+  void *Jm_re = nullptr, *Jm_im = nullptr, *mf_hcs = nullptr, *mf_tab = nullptr;
+  double* mf_src = nullptr;  // host sources of cmcg_solve_multifreq, on the device
+  size_t mf_src_len = 0;
   // CUDA graphs of whole sweeps, captured on first use on a private stream and launched on
   // `stream`; key: sweep kind, mask pointer, boundary data present.
   bool graphs = true;
@@ -423,9 +430,10 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
   R* ACC = (R*)h->ACC;
   const int s = h->s;
   const int L = filter ? h->L_srcf : h->L_src;
-  void* table = filter ? h->tab_srcf : h->tab_src;
+  const int K = with_source ? h->mf_nharm : 0;
+  void* table = filter ? (K > 0 ? h->mf_tab : h->tab_srcf) : h->tab_src;
   const int kind = 2 + (filter ? 1 : 0) + (with_source ? 0 : 2);
-  run_sweep(h, std::make_tuple(kind, (const void*)mask, with_source && h->has_bdata), L, [&](cudaStream_t st) {
+  auto emit = [&](cudaStream_t st) {
   for (int l = 0; l < L; ++l) {
     const int r = l % s;
     StageArgs<R> a = blank<R>();
@@ -444,8 +452,13 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
       }
     }
     if (with_source) {
-      a.jre = (const R*)h->Jre;
-      a.jim = (const R*)h->Jim;
+      a.jre = (const R*)(K > 0 ? h->Jm_re : h->Jre);
+      a.jim = (const R*)(K > 0 ? h->Jm_im : h->Jim);
+      if (K > 0) {
+        a.nharm = K;
+        a.jstride = h->njvec;
+        a.hcs = (const R*)h->mf_hcs + size_t(l) * 2 * K;
+      }
       if (h->has_bdata) {
         a.bre = (const R*)h->Bre;
         a.bim = (const R*)h->Bim;
@@ -460,7 +473,13 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
     stage<R>(h, a, st);
     halo<R>(h, a.out, st);
   }
-  });
+  };
+  if (K > 0) {  // several harmonics: launched directly (their tables change from call to call)
+    emit(h->stream);
+    h->launches += L;
+  } else {
+    run_sweep(h, std::make_tuple(kind, (const void*)mask, with_source && h->has_bdata), L, emit);
+  }
   prof_end(h, pe);
 }
 
@@ -693,6 +712,10 @@ int read_state(cmcg_handle* h) {
 }
 
 
+template <typename R>
+int cg_phase(cmcg_handle* h, const int32_t* mask, double tol, int max_iter);
+int report(cmcg_handle* h, int nused, double tol, float ms, int extra_periods, cmcg_info* info);
+
 // CMCG for problems [0, nused) of the handle (the others are skipped by every
 // kernel); j, e, h: one device pointer per used problem.
 template <typename R>
@@ -708,6 +731,34 @@ int solve_dev(cmcg_handle* h, int nused, const double* const* j_re, const double
   const int32_t* mask = nused < h->nprob ? h->used : nullptr;
   int rc = set_source<R>(h, j_re, j_im, nused);
   if (rc) return rc;
+  if ((rc = cg_phase<R>(h, mask, tol, max_iter))) return rc;
+  // Final filter F_{psi,w} U0 for every used problem.
+  lincomb<R>(h, h->Uw, nullptr, nullptr, 1.0, h->U0, 0.0, nullptr);
+  CK(cudaMemsetAsync(h->Fre, 0, h->nvec * h->rsize, h->stream));
+  CK(cudaMemsetAsync(h->Fim, 0, h->nvec * h->rsize, h->stream));
+  sweep_source<R>(h, true, true, mask);
+  for (int p = 0; p < nused; ++p) {
+    to_ext<R>(h, p, h->Fre, 6, 0, e_re[p], 3, 3);
+    to_ext<R>(h, p, h->Fim, 6, 0, e_im[p], 3, 3);
+    to_ext<R>(h, p, h->Fre, 6, 3, h_re[p], 3, 3);
+    to_ext<R>(h, p, h->Fim, 6, 3, h_im[p], 3, 3);
+  }
+  CK(cudaEventRecord(ev1, h->stream));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  if ((rc = check_err(h))) return rc;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  return report(h, nused, tol, ms, 0, info);
+}
+
+// Algorithms init and cmcg (residual form) on the sources already in place, for the problems
+// of `mask` (nullptr: all); U0 holds the result.
+template <typename R>
+int cg_phase(cmcg_handle* h, const int32_t* mask, double tol, int max_iter) {
+  int rc = CMCG_OK;
   CK(cudaMemsetAsync(h->sc, 0, sizeof(Scalars) * h->nprob, h->stream));
   // Algorithm init: G = P_psi 0, G_T = P* G, G* = G - G_T.
   CK(cudaMemsetAsync(h->Uw, 0, h->nvec * h->rsize, h->stream));
@@ -746,25 +797,12 @@ int solve_dev(cmcg_handle* h, int nused, const double* const* j_re, const double
     rc = read_state(h);
     if (rc) return rc;
   }
-  // Final filter F_{psi,w} U0 for every used problem.
-  lincomb<R>(h, h->Uw, nullptr, nullptr, 1.0, h->U0, 0.0, nullptr);
-  CK(cudaMemsetAsync(h->Fre, 0, h->nvec * h->rsize, h->stream));
-  CK(cudaMemsetAsync(h->Fim, 0, h->nvec * h->rsize, h->stream));
-  sweep_source<R>(h, true, true, mask);
-  for (int p = 0; p < nused; ++p) {
-    to_ext<R>(h, p, h->Fre, 6, 0, e_re[p], 3, 3);
-    to_ext<R>(h, p, h->Fim, 6, 0, e_im[p], 3, 3);
-    to_ext<R>(h, p, h->Fre, 6, 3, h_re[p], 3, 3);
-    to_ext<R>(h, p, h->Fim, 6, 3, h_im[p], 3, 3);
-  }
-  CK(cudaEventRecord(ev1, h->stream));
-  CK(cudaGetLastError());
-  CK(cudaStreamSynchronize(h->stream));
-  if ((rc = check_err(h))) return rc;
-  float ms = 0;
-  cudaEventElapsedTime(&ms, ev0, ev1);
-  cudaEventDestroy(ev0);
-  cudaEventDestroy(ev1);
+  return CMCG_OK;
+}
+
+// Reports of problems [0, nused) after a synchronised solve; extra_periods: filtered sweeps
+// beyond the one of Algorithm cmcg.  Returns the most severe status.
+int report(cmcg_handle* h, int nused, double tol, float ms, int extra_periods, cmcg_info* info) {
   int worst = CMCG_OK;
   for (int p = 0; p < nused; ++p) {
     const Scalars& S = h->sc_host[p];
@@ -778,7 +816,7 @@ int solve_dev(cmcg_handle* h, int nused, const double* const* j_re, const double
     }
     if (info) {
       info[p].iters = S.iters;
-      info[p].periods = 3 + 2 * S.iters;
+      info[p].periods = 3 + 2 * S.iters + extra_periods;
       info[p].steps_per_period = h->P[p].M;
       info[p].status = st;
       info[p].rel_residual = S.rr0 > 0 ? std::sqrt(std::max(S.rr, 0.0) / S.rr0) : 0.0;
@@ -787,6 +825,109 @@ int solve_dev(cmcg_handle* h, int nused, const double* const* j_re, const double
     }
   }
   return worst;
+}
+
+// Several frequencies in one solve (the one-shot remark of the Conclusion, Section 7): the
+// handle's omega is the base frequency w0; harmonic k_h w0 has the source j_h.  CMCG runs once on
+// the period T0 = 2 pi / w0 of the summed source; then one filtered sweep from U0 per harmonic,
+// each with the filter weights of its frequency k_h w0 over T0 (Eq. filter, Section 5.4),
+// returns that frequency's time-harmonic field.  Sources j_h and results are device pointers;
+// `sink(h_index)` runs after harmonic h's results are written (host entry points copy them out).
+template <typename R, typename Sink>
+int solve_multi_dev(cmcg_handle* h, int K, const int* harm, const double* const* j_re, const double* const* j_im,
+                    double tol, int max_iter, double* e_re, double* e_im, double* h_re, double* h_im, Sink&& sink,
+                    cmcg_info* info) {
+  Prob& P = h->P[0];
+  const size_t vb = size_t(h->njvec) * h->rsize;
+  if (K > h->mf_cap) {  // K sources and the per-launch harmonic coefficients (kept for later calls)
+    if (h->Jm_re) cudaFree(h->Jm_re);
+    if (h->Jm_im) cudaFree(h->Jm_im);
+    if (h->mf_hcs) cudaFree(h->mf_hcs);
+    h->Jm_re = h->Jm_im = h->mf_hcs = nullptr;
+    h->mf_cap = 0;
+    if (cudaMalloc(&h->Jm_re, vb * K) != cudaSuccess || cudaMalloc(&h->Jm_im, vb * K) != cudaSuccess ||
+        cudaMalloc(&h->mf_hcs, size_t(h->L_srcf) * 2 * K * h->rsize) != cudaSuccess)
+      return CMCG_ERR_OUT_OF_MEMORY;
+    h->mf_cap = K;
+    h->bytes += 2 * vb * K + size_t(h->L_srcf) * 2 * K * h->rsize;
+  }
+  if (!h->mf_tab) {
+    if (cudaMalloc(&h->mf_tab, size_t(h->L_srcf) * sizeof(StageCoef<R>)) != cudaSuccess) return CMCG_ERR_OUT_OF_MEMORY;
+    h->bytes += size_t(h->L_srcf) * sizeof(StageCoef<R>);
+  }
+  // cos / sin of every harmonic at every launch's stage time (the stage offsets of Algorithms rk2 / rk4)
+  const int s = h->s;
+  static const double off4[4] = {0.0, 0.5, 0.5, 1.0}, off2[2] = {0.0, 0.5};
+  std::vector<R> hcs(static_cast<size_t>(h->L_srcf) * 2 * K);
+  for (int l = 0; l < h->L_srcf; ++l) {
+    const int m = l / s, r = l % s;
+    const double t = (m + (s == 4 ? off4[r] : off2[r])) * P.dt;
+    for (int k = 0; k < K; ++k) {
+      hcs[(size_t(l) * K + k) * 2] = R(std::cos(harm[k] * P.omega * t));
+      hcs[(size_t(l) * K + k) * 2 + 1] = R(std::sin(harm[k] * P.omega * t));
+    }
+  }
+  CK(cudaMemcpyAsync(h->mf_hcs, hcs.data(), hcs.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
+  cudaEvent_t ev0, ev1;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, h->stream));
+  for (int k = 0; k < K; ++k) {
+    void* jr = static_cast<char*>(h->Jm_re) + vb * k;
+    void* ji = static_cast<char*>(h->Jm_im) + vb * k;
+    to_int<R>(h, 0, j_re[k], 3, jr, 3, 3, h->inv_eps);
+    if (j_im && j_im[k]) to_int<R>(h, 0, j_im[k], 3, ji, 3, 3, h->inv_eps);
+    else CK(cudaMemsetAsync(ji, 0, vb, h->stream));
+  }
+  h->used_host[0] = 1;  // the problem takes part (read by the first reduction of the CG phase)
+  CK(cudaMemcpyAsync(h->used, h->used_host, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  h->mf_nharm = K;
+  int rc = cg_phase<R>(h, nullptr, tol, max_iter);
+  for (int k = 0; rc == CMCG_OK && k < K; ++k) {
+    // filter weights of the frequency harm[k] w0 over T0, in the filtered sweep's table
+    Prob Pk = P;
+    Pk.omega = harm[k] * P.omega;
+    filter_weights(Pk, s);
+    std::vector<StageCoef<R>> tsf(static_cast<size_t>(h->L_srcf));
+    for (int l = 0; l < h->L_srcf; ++l) {
+      const int m = l / s, r = l % s;
+      StageCoef<R> c;
+      std::memset(&c, 0, sizeof(c));
+      if (m < Pk.M || (m == Pk.M && r == 0)) {
+        c.active = 1;
+        classic_coef<R>(s, r, Pk.dt, m * Pk.dt, Pk.omega, c);
+        if (r == 0) {
+          c.fa_re = R(Pk.fa[m].real());
+          c.fa_im = R(Pk.fa[m].imag());
+          c.fb_re = R(Pk.fb[m].real());
+          c.fb_im = R(Pk.fb[m].imag());
+        }
+      }
+      tsf[size_t(l)] = c;
+    }
+    CK(cudaMemcpyAsync(h->mf_tab, tsf.data(), tsf.size() * sizeof(StageCoef<R>), cudaMemcpyHostToDevice, h->stream));
+    lincomb<R>(h, h->Uw, nullptr, nullptr, 1.0, h->U0, 0.0, nullptr);
+    CK(cudaMemsetAsync(h->Fre, 0, h->nvec * h->rsize, h->stream));
+    CK(cudaMemsetAsync(h->Fim, 0, h->nvec * h->rsize, h->stream));
+    sweep_source<R>(h, true, true, nullptr);
+    to_ext<R>(h, 0, h->Fre, 6, 0, e_re, 3, 3);
+    to_ext<R>(h, 0, h->Fim, 6, 0, e_im, 3, 3);
+    to_ext<R>(h, 0, h->Fre, 6, 3, h_re, 3, 3);
+    to_ext<R>(h, 0, h->Fim, 6, 3, h_im, 3, 3);
+    rc = sink(k);
+    CK(cudaStreamSynchronize(h->stream));  // the host filter table is rebuilt for the next harmonic
+  }
+  h->mf_nharm = 0;
+  if (rc) return rc;
+  CK(cudaEventRecord(ev1, h->stream));
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));
+  if ((rc = check_err(h))) return rc;
+  float ms = 0;
+  cudaEventElapsedTime(&ms, ev0, ev1);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  return report(h, 1, tol, ms, K - 1, info);
 }
 
 // Limiting amplitude ("full wave", Section 6): U = P_psi^periods 0, then
@@ -822,7 +963,8 @@ void free_all(cmcg_handle* h) {
   drop_graphs(h);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->cap_stream = nullptr;
-  void* ptrs[] = {h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
+  void* ptrs[] = {h->Jm_re, h->Jm_im, h->mf_hcs, h->mf_tab, h->mf_src,
+                  h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
                   h->Fre, h->Fim, h->Jre, h->Jim, h->Bre, h->Bim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
                   h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
                   h->ext0, h->ext1, h->ext2, h->ext3, h->used, h->err, h->halo_dst, h->halo_src, h->g_in,
@@ -1638,6 +1780,52 @@ int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* co
 }
 
 int64_t cmcg_device_bytes(const cmcg_handle* h) { return h ? int64_t(h->bytes) : 0; }
+
+int cmcg_solve_multifreq(cmcg_handle* h, int nharm, const int* harmonics, const double* const* j_re,
+                         const double* const* j_im, double tol, int max_iter, double* const* e_re,
+                         double* const* e_im, double* const* h_re, double* const* h_im, cmcg_info* info) {
+  if (!h || h->nprob != 1 || h->coupled || nharm < 1 || nharm > 64 || !harmonics || !j_re || !e_re || !e_im ||
+      !h_re || !h_im || !(tol >= 0) || max_iter < 0)
+    return CMCG_ERR_INVALID_ARG;
+  for (int k = 0; k < nharm; ++k)
+    if (harmonics[k] < 1 || !j_re[k] || !e_re[k] || !e_im[k] || !h_re[k] || !h_im[k]) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  const size_t nj = size_t(h->nt_total) * 3 * h->np;
+  // the host sources go to a device buffer of 2 nharm sources, kept for later calls
+  const size_t need = 2 * size_t(nharm) * nj;
+  if (need > h->mf_src_len) {
+    if (h->mf_src) cudaFree(h->mf_src);
+    h->mf_src = nullptr;
+    h->mf_src_len = 0;
+    if (cudaMalloc((void**)&h->mf_src, need * sizeof(double)) != cudaSuccess) return CMCG_ERR_OUT_OF_MEMORY;
+    h->mf_src_len = need;
+    h->bytes += need * sizeof(double);
+  }
+  std::vector<const double*> djr(static_cast<size_t>(nharm)), dji(static_cast<size_t>(nharm), nullptr);
+  for (int k = 0; k < nharm; ++k) {
+    double* re = h->mf_src + 2 * size_t(k) * nj;
+    CK(cudaMemcpyAsync(re, j_re[k], nj * 8, cudaMemcpyHostToDevice, h->stream));
+    djr[size_t(k)] = re;
+    if (j_im && j_im[k]) {
+      CK(cudaMemcpyAsync(re + nj, j_im[k], nj * 8, cudaMemcpyHostToDevice, h->stream));
+      dji[size_t(k)] = re + nj;
+    }
+  }
+  // results of each harmonic through the staging vectors: e in ext0 (re, im), h in ext1
+  double *de_re = h->ext0, *de_im = h->ext0 + nj, *dh_re = h->ext1, *dh_im = h->ext1 + nj;
+  auto sink = [&](int k) -> int {
+    CK(cudaMemcpyAsync(e_re[k], de_re, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(e_im[k], de_im, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h_re[k], dh_re, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h_im[k], dh_im, nj * 8, cudaMemcpyDeviceToHost, h->stream));
+    return CMCG_OK;
+  };
+  return DISPATCH(h,
+                  solve_multi_dev<float>(h, nharm, harmonics, djr.data(), dji.data(), tol, max_iter, de_re, de_im,
+                                         dh_re, dh_im, sink, info),
+                  solve_multi_dev<double>(h, nharm, harmonics, djr.data(), dji.data(), tol, max_iter, de_re, de_im,
+                                          dh_re, dh_im, sink, info));
+}
 
 int cmcg_solve_device(cmcg_handle* h, const double* j_re, const double* j_im, double tol, int max_iter, double* e_re,
                       double* e_im, double* h_re, double* h_im, cmcg_info* info) {

@@ -145,6 +145,11 @@ struct StageArgs {
   int64_t nti;
   int32_t* err;  // device status word: a stage kernel whose bounded wait ran out ORs in 1 (null: not recorded)
   int32_t sigma;  // nonzero: some tetrahedron has a conductivity (sigma/eps in gvol item 11)
+  // Several harmonics in one sweep (nharm > 0): the source is sum_h hcs[2h] J_re,h - hcs[2h+1] J_im,h
+  // with J_h = jre / jim + h * jstride (hcs: this launch's cos / sin of the harmonics at the stage time).
+  int32_t nharm;
+  int64_t jstride;
+  const R* hcs;
 };
 
 // Kernel launchers, one translation unit per order.

@@ -90,6 +90,40 @@ __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.w
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// The source on the E rows, added by the thread that computes Phi_E (Eq. ode_system): at the
+// stage time, Re(J e^{i w t}) = s_cos J_re - s_sin J_im, or, in a sweep driven at several
+// harmonics of a base frequency (a.nharm > 0), the sum over the harmonics of
+// hcs[2h] J_re,h - hcs[2h+1] J_im,h.  Output nodes n0 .. n0 + NN - 1 of (tile, lane).
+template <typename R, int NN>
+__device__ __forceinline__ void add_source(R (&phi)[3][NN], const StageArgs<R>& a, const StageCoef<R>& cf,
+                                           int64_t tile, int lane, int n0) {
+  constexpr int NP = NPQ;
+  const int64_t joff = tile * (3 * NP * TILE) + lane;
+  if (a.nharm <= 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int ii = 0; ii < NN; ++ii) {
+        const int64_t o = joff + (c * NP + n0 + ii) * TILE;
+        phi[c][ii] += cf.s_cos * a.jre[o] - cf.s_sin * a.jim[o];
+      }
+    return;
+  }
+#pragma unroll 1
+  for (int hh = 0; hh < a.nharm; ++hh) {
+    const R sc = a.hcs[2 * hh], ss = a.hcs[2 * hh + 1];
+    const R* jr = a.jre + hh * a.jstride;
+    const R* ji = a.jim + hh * a.jstride;
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int ii = 0; ii < NN; ++ii) {
+        const int64_t o = joff + (c * NP + n0 + ii) * TILE;
+        phi[c][ii] += sc * jr[o] - ss * ji[o];
+      }
+  }
+}
+
 // MINB: minimum resident blocks per SM requested from the compiler (caps registers at
 // 65536 / (MINB * STAGE_THREADS)); the forms are timed per handle (see api.cu).
 template <typename R, int MINB>
@@ -267,16 +301,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
 #pragma unroll
       for (int n = 0; n < NP; ++n) phi[c][n] -= so * ev[(c * NP + n) * TILE];
   }
-  if (half && a.jre) {  // source on the E rows
-    const int64_t joff = tile * (3 * NP * TILE) + lane;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        const int64_t o = joff + (c * NP + n) * TILE;
-        phi[c][n] += cf.s_cos * a.jre[o] - cf.s_sin * a.jim[o];
-      }
-  }
+  if (half && a.jre) add_source<R, NP>(phi, a, cf, tile, lane, 0);  // source on the E rows
   if (a.bre) {  // impedance-face data, lifted onto this thread's output rows (source sweeps only)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -531,16 +556,7 @@ __device__ __forceinline__ void quad_stage(const StageArgs<R>& a) {
 #pragma unroll
       for (int ii = 0; ii < NH; ++ii) phi[c][ii] -= so * ev[(c * NP + I0 + ii) * TILE];
   }
-  if (half && a.jre) {  // source on the E rows
-    const int64_t joff = tile * (3 * NP * TILE) + lane;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int64_t o = joff + (c * NP + I0 + ii) * TILE;
-        phi[c][ii] += cf.s_cos * a.jre[o] - cf.s_sin * a.jim[o];
-      }
-  }
+  if (half && a.jre) add_source<R, NH>(phi, a, cf, tile, lane, I0);  // source on the E rows
   if (a.bre) {  // impedance-face data on this thread's output rows
 #pragma unroll
     for (int c = 0; c < 3; ++c)

@@ -518,16 +518,7 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
 #pragma unroll
       for (int n = 0; n < NP; ++n) phi[c][n] -= so * ev[(c * NP + n) * TILE];
   }
-  if (half && a.jre) {  // source on the E rows
-    const int64_t joff = tile * (3 * NP * TILE) + lane;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        const int64_t o = joff + (c * NP + n) * TILE;
-        phi[c][n] += cf.s_cos * a.jre[o] - cf.s_sin * a.jim[o];
-      }
-  }
+  if (half && a.jre) add_source<R, NP>(phi, a, cf, tile, lane, 0);  // source on the E rows
   if (a.bre) {  // impedance-face data on this thread's output rows (source sweeps only)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -888,16 +879,7 @@ __global__ void __launch_bounds__(T4_THREADS, MINB) dg_stage_tc4(const StageArgs
 #pragma unroll
       for (int ii = 0; ii < NH; ++ii) phi[c][ii] -= so * ev[(c * NP + n0 + ii) * TILE];
   }
-  if (half && a.jre) {  // source on the E rows
-    const int64_t joff = tile * (3 * NP * TILE) + lane;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int64_t o = joff + (c * NP + n0 + ii) * TILE;
-        phi[c][ii] += cf.s_cos * a.jre[o] - cf.s_sin * a.jim[o];
-      }
-  }
+  if (half && a.jre) add_source<R, NH>(phi, a, cf, tile, lane, n0);  // source on the E rows
   if (a.bre) {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
