@@ -378,6 +378,29 @@ int cmcg_solve_batch_n(cmcg_handle* h, int n, const double* const* j_re, const d
                        int max_iter, double* const* e_re, double* const* e_im, double* const* h_re,
                        double* const* h_im, cmcg_info* info);
 
+/* Continuous batching on a batch handle (the serving runtime's engine; the paper
+ * has no counterpart).  Problem p of the handle is slot p.
+ *   cmcg_slot_admit: starts a request in an empty slot: host j_re, j_im
+ *     (double[nt_p][3][Np]; j_im may be NULL) are copied before it returns.
+ *   cmcg_slot_round: advances every busy slot by one step of its solve in the
+ *     same sweeps: Algorithm init for admitted slots, one CG iteration
+ *     (Algorithm grad and the update of Algorithm cmcg) for iterating slots, the
+ *     final filter for slots whose CG stopped (converged, broke down, or reached
+ *     max_iter); done (NULL or int[nprob]) receives 1 for the slots whose result
+ *     became ready in this round.  Requests admitted between rounds join the
+ *     next round while the others continue.
+ *   cmcg_slot_take: copies a ready result (e, h as in cmcg_solve; any pointer
+ *     may be NULL) and its report, empties the slot and returns its status.
+ *   cmcg_slot_state: 0 empty, 1 admitted, 2 iterating, 3 filter pending,
+ *     4 result ready (CMCG_ERR_INVALID_ARG for a bad slot).
+ * A slot's arithmetic is that of cmcg_solve of the same problem alone with
+ * the same kernel form (stage_variant): results do not depend on the other
+ * slots.  Not for sharded handles.  tol and max_iter apply to every slot. */
+int cmcg_slot_admit(cmcg_handle* h, int slot, const double* j_re, const double* j_im);
+int cmcg_slot_round(cmcg_handle* h, double tol, int max_iter, int* done);
+int cmcg_slot_take(cmcg_handle* h, int slot, double* e_re, double* e_im, double* h_re, double* h_im, cmcg_info* info);
+int cmcg_slot_state(const cmcg_handle* h, int slot);
+
 /* Device memory held by a handle, in bytes (the figure cmcg_create checks
  * against hbm_budget_bytes). */
 int64_t cmcg_device_bytes(const cmcg_handle* h);
@@ -460,21 +483,23 @@ int cmcg_measure_peaks(int device, double* fp32_tflops, double* tf32_tflops);
  *
  * A server holds registered models (mesh, eps, mu, omega, order) and a queue
  * of requests (one source each).  Worker threads, each with its own CUDA
- * stream, take the oldest request, gather up to the model's batch capacity of
- * queued requests of the same model (waiting at most max_wait_ms), and solve
- * them together (cmcg_solve_batch_n) on a pooled batch handle; batches of
+ * stream, take the model of the oldest request (waiting at most max_wait_ms
+ * for more of it) and run a pooled batch handle of that model as slots
+ * (cmcg_slot_*): each round advances every busy slot by one step of its solve,
+ * and between rounds queued requests of the model take the slots that finished
+ * requests left free, while the other slots keep iterating.  Handles of
  * different workers run concurrently.  New handles are created only while the
  * server's device memory stays within hbm_budget_bytes (0 = no limit);
- * otherwise a batch waits for a pooled handle.  Every handle of a model uses
+ * otherwise a worker waits for a pooled handle.  Every handle of a model uses
  * the kernel form chosen when the model was registered, so a request's result
- * is the one it gets when solved alone, whatever shares its batch.  Requests
+ * is the one it gets when solved alone, whatever shares its handle.  Requests
  * carry a volume source only (no impedance-face data). */
 typedef struct cmcg_server cmcg_server;
 
 typedef struct cmcg_server_options {
   int device;
   int precision;      /* CMCG_FP32 (default) or CMCG_FP64 */
-  int max_batch;      /* default batch capacity per model (default 8) */
+  int max_batch;      /* default slots per handle of a model (default 8) */
   int workers;        /* worker threads / streams (default 2) */
   double max_wait_ms; /* micro-batching window (default 2) */
   double tol;         /* CG tolerance of every request (default 1e-6) */

@@ -132,6 +132,10 @@ def _load() -> C.CDLL:
         "cmcg_profile_enable": (C.c_int, [_vp, C.c_int]),
         "cmcg_measure_peaks": (C.c_int, [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
         "cmcg_partition_slabs": (C.c_int, [C.POINTER(cmcg_mesh), C.c_int, C.c_int, C.POINTER(C.c_int32)]),
+        "cmcg_slot_admit": (C.c_int, [_vp, C.c_int, _dp, _dp]),
+        "cmcg_slot_round": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
+        "cmcg_slot_take": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp, C.POINTER(cmcg_info)]),
+        "cmcg_slot_state": (C.c_int, [_vp, C.c_int]),
         "cmcg_solve_multifreq": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_dp), C.POINTER(_dp),
                                            C.c_double, C.c_int, C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp),
                                            C.POINTER(_dp), C.POINTER(cmcg_info)]),
@@ -160,7 +164,8 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_device_bytes", "cmcg_fw_solve", "cmcg_fw_solve_batch", "cmcg_set_boundary_data", "cmcg_server_default_options", "cmcg_server_create", "cmcg_server_add_model",
             "cmcg_server_submit", "cmcg_server_poll", "cmcg_server_stats", "cmcg_server_destroy",
             "cmcg_measure_peaks", "cmcg_set_conductivity", "cmcg_partition_slabs", "cmcg_shard_plan",
-            "cmcg_create_sharded", "cmcg_solve_multifreq")
+            "cmcg_create_sharded", "cmcg_solve_multifreq", "cmcg_slot_admit", "cmcg_slot_round", "cmcg_slot_take",
+            "cmcg_slot_state")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
 
@@ -292,6 +297,35 @@ def cmcg_create(mesh: MeshArrays, eps, mu, omega: float, opt: cmcg_options) -> H
     _check(_lib.cmcg_get_sizes(out, C.byref(nt), C.byref(np_), C.byref(steps), C.byref(dt), C.byref(fl)),
            "cmcg_get_sizes")
     return Handle(out.value, nt.value, np_.value, steps.value, dt.value)
+
+
+def cmcg_slot_admit(h: Handle, slot: int, j_re, j_im=None) -> None:
+    nt = h.problems[slot][0]
+    jr = _f64(j_re, (nt, 3, h.np), "j_re")
+    ji = None if j_im is None else _f64(j_im, (nt, 3, h.np), "j_im")
+    _check(_lib.cmcg_slot_admit(h.ptr, int(slot), _ptr(jr), _ptr(ji)), "cmcg_slot_admit")
+
+
+def cmcg_slot_round(h: Handle, tol: float, max_iter: int):
+    """One round; returns the slots whose result became ready."""
+    n = len(h.problems)
+    done = (C.c_int * n)()
+    _check(_lib.cmcg_slot_round(h.ptr, float(tol), int(max_iter), done), "cmcg_slot_round")
+    return [p for p in range(n) if done[p]]
+
+
+def cmcg_slot_take(h: Handle, slot: int):
+    """(e, h) complex (nt, 3, Np) and the report of a ready slot; the slot becomes empty."""
+    nt = h.problems[slot][0]
+    er, ei, hr, hi = (np.empty((nt, 3, h.np)) for _ in range(4))
+    info = cmcg_info()
+    rc = _lib.cmcg_slot_take(h.ptr, int(slot), _ptr(er), _ptr(ei), _ptr(hr), _ptr(hi), C.byref(info))
+    _check(rc, "cmcg_slot_take", allow_not_converged=True)
+    return er + 1j * ei, hr + 1j * hi, info
+
+
+def cmcg_slot_state(h: Handle, slot: int) -> int:
+    return int(_lib.cmcg_slot_state(h.ptr, int(slot)))
 
 
 def cmcg_solve_multifreq(h: Handle, harmonics, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 1000):

@@ -121,6 +121,11 @@ struct cmcg_handle {
   void *Jm_re = nullptr, *Jm_im = nullptr, *mf_hcs = nullptr, *mf_tab = nullptr;
   double* mf_src = nullptr;  // host sources of cmcg_solve_multifreq, on the device
   size_t mf_src_len = 0;
+  // Slots (continuous batching, cmcg_slot_*): phase of every problem and the per-phase masks.
+  std::vector<int> slot_phase;
+  std::vector<cmcg_info> slot_info;
+  int32_t* slot_masks = nullptr;       // device [3][nprob]: admitted, adjoint sweep, filter pending
+  int32_t* slot_masks_host = nullptr;  // pinned
   // CUDA graphs of whole sweeps, captured on first use on a private stream and launched on
   // `stream`; key: sweep kind, mask pointer, boundary data present.
   bool graphs = true;
@@ -930,6 +935,153 @@ int solve_multi_dev(cmcg_handle* h, int K, const int* harm, const double* const*
   return report(h, 1, tol, ms, K - 1, info);
 }
 
+// ------------------------------------------------------------------------------------------
+// Slots: continuous batching on a batch handle.  Problem p is slot p; its phase is EMPTY,
+// ADMITTED (source in place, Algorithm init pending), CG (iterating), FINAL (its CG stopped:
+// filter pending) or DONE (result staged in ext0 / ext1 at the problem's offsets).  A round runs
+// every phase's work with the problems of that phase masked in, in an order that keeps each
+// problem's sequence of operations that of solve_dev: the source sweep of admitted slots, the
+// forward sweep of iterating slots, one adjoint sweep for both, the CG updates of iterating
+// slots, the reductions of Algorithm init for admitted slots (after the CG updates, which they
+// must not take part in), and the filtered sweep of FINAL slots.
+enum { SLOT_EMPTY = 0, SLOT_ADMITTED = 1, SLOT_CG = 2, SLOT_FINAL = 3, SLOT_DONE = 4 };
+
+int slot_setup(cmcg_handle* h) {
+  if (h->slot_masks) return CMCG_OK;
+  if (cudaMalloc((void**)&h->slot_masks, sizeof(int32_t) * 3 * h->nprob) != cudaSuccess ||
+      cudaMallocHost((void**)&h->slot_masks_host, sizeof(int32_t) * 3 * h->nprob) != cudaSuccess)
+    return CMCG_ERR_OUT_OF_MEMORY;
+  h->slot_phase.assign(size_t(h->nprob), SLOT_EMPTY);
+  h->slot_info.assign(size_t(h->nprob), cmcg_info{});
+  for (int p = 0; p < h->nprob; ++p) h->pactive_host[p] = 0;
+  CK(cudaMemcpyAsync(h->pactive, h->pactive_host, sizeof(int32_t) * h->nprob, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return CMCG_OK;
+}
+
+template <typename R>
+void zero_tiles(cmcg_handle* h, void* v, int p) {
+  const Prob& P = h->P[size_t(p)];
+  const size_t per_tile = size_t(6) * h->np * TILE * h->rsize;
+  cudaMemsetAsync(static_cast<char*>(v) + size_t(P.tile0) * per_tile, 0, size_t(P.ntiles) * per_tile, h->stream);
+}
+
+template <typename R>
+int slot_round_dev(cmcg_handle* h, double tol, int max_iter, int* done) {
+  const int n = h->nprob;
+  int32_t* mh = h->slot_masks_host;  // [admitted | adjoint | final]
+  int32_t* m_init = h->slot_masks;
+  int32_t* m_adj = h->slot_masks + n;
+  int32_t* m_fin = h->slot_masks + 2 * n;
+  bool any_init = false, any_cg = false, any_fin = false;
+  for (int p = 0; p < n; ++p) {
+    const int ph = h->slot_phase[size_t(p)];
+    const bool cg = ph == SLOT_CG && h->pactive_host[p];
+    mh[p] = ph == SLOT_ADMITTED;
+    mh[n + p] = mh[p] || cg;
+    mh[2 * n + p] = ph == SLOT_FINAL;
+    any_init = any_init || mh[p];
+    any_cg = any_cg || cg;
+    any_fin = any_fin || mh[2 * n + p];
+    if (done) done[p] = 0;
+  }
+  CK(cudaMemcpyAsync(h->slot_masks, mh, sizeof(int32_t) * 3 * n, cudaMemcpyHostToDevice, h->stream));
+  if (any_init) {  // Algorithm init, first half: G = P_psi 0 (kept in A)
+    for (int p = 0; p < n; ++p)
+      if (mh[p]) {
+        zero_tiles<R>(h, h->Uw, p);
+        CK(cudaMemsetAsync(h->sc + p, 0, sizeof(Scalars), h->stream));
+      }
+    sweep_source<R>(h, true, false, m_init);
+    launch_lincomb3_masked<R>((R*)h->A, nullptr, nullptr, 1.0, (const R*)h->Uw, 0.0, nullptr, h->nvec, h->np, h->tprob,
+                              m_init, h->stream);
+    h->launches++;
+  }
+  if (any_cg) {  // Algorithm grad on D: W_T = P D - D (iterating slots only: admitted slots hold G in Uw)
+    sweep_free<R>(h, false, h->pactive);
+    launch_lincomb3_masked<R>((R*)h->WT, (R*)h->Uw, nullptr, 1.0, (const R*)h->Uw, -1.0, (const R*)h->D, h->nvec,
+                              h->np, h->tprob, h->pactive, h->stream);
+    h->launches++;
+  }
+  if (any_init || any_cg) sweep_free<R>(h, true, m_adj);  // P* G (admitted), P* W_T (iterating)
+  if (any_cg) {  // A = P* W_T - W_T and the CG update, as in solve_dev
+    launch_cg_after_adjoint<R>(h->q, (const R*)h->Uw, (const R*)h->WT, (R*)h->A, (const R*)h->D, h->wdot, h->partials,
+                               h->bt, h->pactive, h->stream);
+    launch_finalize(h->partials, h->bt, h->sc, h->pactive, nullptr, 1, tol, h->stream);
+    launch_cg_update<R>(h->q, (R*)h->U0, (R*)h->Rv, (const R*)h->D, (const R*)h->A, h->wdot, h->sc, h->partials, h->bt,
+                        h->pactive, h->stream);
+    launch_finalize(h->partials, h->bt, h->sc, h->pactive, nullptr, 2, tol, h->stream);
+    launch_cg_direction<R>((R*)h->D, (R*)h->Uw, (const R*)h->Rv, h->sc, h->tprob, h->pactive, h->nvec, h->np,
+                           h->stream);
+    h->launches += 5;
+  }
+  if (any_init) {  // Algorithm init, second half: R = D = G* = G - P* G, U0 = 0, |R|^2
+    launch_lincomb3_masked<R>((R*)h->Rv, (R*)h->D, (R*)h->Uw, 1.0, (const R*)h->A, -1.0, (const R*)h->Uw, h->nvec,
+                              h->np, h->tprob, m_init, h->stream);
+    for (int p = 0; p < n; ++p)
+      if (mh[p]) zero_tiles<R>(h, h->U0, p);
+    launch_dot<R>(h->q, (const R*)h->Rv, (const R*)h->Rv, h->wdot, h->partials, h->bt, h->stream);
+    launch_finalize(h->partials, h->bt, h->sc, h->pactive, m_init, 4, tol, h->stream);
+    h->launches += 3;
+  }
+  if (any_fin) {  // the final filter F_{psi,w} U0
+    launch_lincomb3_masked<R>((R*)h->Uw, nullptr, nullptr, 1.0, (const R*)h->U0, 0.0, nullptr, h->nvec, h->np, h->tprob,
+                              m_fin, h->stream);
+    h->launches++;
+    for (int p = 0; p < n; ++p)
+      if (mh[2 * n + p]) {
+        zero_tiles<R>(h, h->Fre, p);
+        zero_tiles<R>(h, h->Fim, p);
+      }
+    sweep_source<R>(h, true, true, m_fin);
+    const size_t half = size_t(h->nt_total) * 3 * h->np;
+    for (int p = 0; p < n; ++p)
+      if (mh[2 * n + p]) {
+        const size_t off = size_t(h->P[size_t(p)].ext0) * 3 * h->np;
+        to_ext<R>(h, p, h->Fre, 6, 0, h->ext0 + off, 3, 3);
+        to_ext<R>(h, p, h->Fim, 6, 0, h->ext0 + half + off, 3, 3);
+        to_ext<R>(h, p, h->Fre, 6, 3, h->ext1 + off, 3, 3);
+        to_ext<R>(h, p, h->Fim, 6, 3, h->ext1 + half + off, 3, 3);
+      }
+  }
+  CK(cudaGetLastError());
+  int rc = read_state(h);
+  if (rc) return rc;
+  bool flip = false;
+  for (int p = 0; p < n; ++p) {
+    int& ph = h->slot_phase[size_t(p)];
+    const Scalars& S = h->sc_host[p];
+    if (ph == SLOT_FINAL) {
+      int st = S.status;
+      const bool conv = S.rr0 > 0 ? std::sqrt(std::max(S.rr, 0.0)) <= tol * std::sqrt(S.rr0) : true;
+      if (st == CMCG_OK && !conv) st = CMCG_NOT_CONVERGED;
+      cmcg_info& I = h->slot_info[size_t(p)];
+      I = cmcg_info{};
+      I.iters = S.iters;
+      I.periods = 3 + 2 * S.iters;
+      I.steps_per_period = h->P[size_t(p)].M;
+      I.status = st;
+      I.rel_residual = S.rr0 > 0 ? std::sqrt(std::max(S.rr, 0.0) / S.rr0) : 0.0;
+      I.dt = h->P[size_t(p)].dt;
+      ph = SLOT_DONE;
+      if (done) done[p] = 1;
+    } else if (ph == SLOT_ADMITTED) {
+      ph = h->pactive_host[p] ? SLOT_CG : SLOT_FINAL;
+    } else if (ph == SLOT_CG) {
+      if (h->pactive_host[p] && S.iters >= max_iter) {  // stop at max_iter: the last iterate is filtered
+        h->pactive_host[p] = 0;
+        flip = true;
+      }
+      if (!h->pactive_host[p]) ph = SLOT_FINAL;
+    }
+  }
+  if (flip) {
+    CK(cudaMemcpyAsync(h->pactive, h->pactive_host, sizeof(int32_t) * n, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return CMCG_OK;
+}
+
 // Limiting amplitude ("full wave", Section 6): U = P_psi^periods 0, then
 // F_psi U, for every problem of the handle.
 template <typename R>
@@ -967,7 +1119,7 @@ void free_all(cmcg_handle* h) {
                   h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
                   h->Fre, h->Fim, h->Jre, h->Jim, h->Bre, h->Bim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
                   h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
-                  h->ext0, h->ext1, h->ext2, h->ext3, h->used, h->err, h->halo_dst, h->halo_src, h->g_in,
+                  h->ext0, h->ext1, h->ext2, h->ext3, h->used, h->err, h->slot_masks, h->halo_dst, h->halo_src, h->g_in,
                   h->g_out, h->inv_eps_g};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -975,6 +1127,7 @@ void free_all(cmcg_handle* h) {
   if (h->pactive_host) cudaFreeHost(h->pactive_host);
   if (h->used_host) cudaFreeHost(h->used_host);
   if (h->err_host) cudaFreeHost(h->err_host);
+  if (h->slot_masks_host) cudaFreeHost(h->slot_masks_host);
   for (auto& e : h->prof_ev) {
     cudaEventDestroy(e.a);
     cudaEventDestroy(e.b);
@@ -1780,6 +1933,74 @@ int cmcg_solve_batch(cmcg_handle* h, const double* const* j_re, const double* co
 }
 
 int64_t cmcg_device_bytes(const cmcg_handle* h) { return h ? int64_t(h->bytes) : 0; }
+
+int cmcg_slot_state(const cmcg_handle* h, int slot) {
+  if (!h || h->coupled || slot < 0 || slot >= h->nprob) return CMCG_ERR_INVALID_ARG;
+  return h->slot_phase.empty() ? SLOT_EMPTY : h->slot_phase[size_t(slot)];
+}
+
+int cmcg_slot_admit(cmcg_handle* h, int slot, const double* j_re, const double* j_im) {
+  if (!h || h->coupled || slot < 0 || slot >= h->nprob || !j_re) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  int rc = slot_setup(h);
+  if (rc) return rc;
+  if (h->slot_phase[size_t(slot)] != SLOT_EMPTY) return CMCG_ERR_INVALID_ARG;
+  const Prob& P = h->P[size_t(slot)];
+  const size_t half = size_t(h->nt_total) * 3 * h->np;
+  const size_t off = size_t(P.ext0) * 3 * h->np, cnt = size_t(P.nt) * 3 * h->np;
+  const double* jr = h->ext3 + off;
+  const double* ji = nullptr;
+  CK(cudaMemcpyAsync(h->ext3 + off, j_re, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+  if (j_im) {
+    CK(cudaMemcpyAsync(h->ext3 + half + off, j_im, cnt * 8, cudaMemcpyHostToDevice, h->stream));
+    ji = h->ext3 + half + off;
+  }
+  if (h->prec == CMCG_FP32) {
+    to_int<float>(h, slot, jr, 3, h->Jre, 3, 3, h->inv_eps);
+    if (ji) to_int<float>(h, slot, ji, 3, h->Jim, 3, 3, h->inv_eps);
+  } else {
+    to_int<double>(h, slot, jr, 3, h->Jre, 3, 3, h->inv_eps);
+    if (ji) to_int<double>(h, slot, ji, 3, h->Jim, 3, 3, h->inv_eps);
+  }
+  if (!ji) {
+    const size_t per_tile = size_t(3) * h->np * TILE * h->rsize;
+    CK(cudaMemsetAsync(static_cast<char*>(h->Jim) + size_t(P.tile0) * per_tile, 0, size_t(P.ntiles) * per_tile,
+                       h->stream));
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(h->stream));  // the host source may be reused when this returns
+  h->slot_phase[size_t(slot)] = SLOT_ADMITTED;
+  return CMCG_OK;
+}
+
+int cmcg_slot_round(cmcg_handle* h, double tol, int max_iter, int* done) {
+  if (!h || h->coupled || !(tol >= 0) || max_iter < 0) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  int rc = slot_setup(h);
+  if (rc) return rc;
+  rc = DISPATCH(h, slot_round_dev<float>(h, tol, max_iter, done), slot_round_dev<double>(h, tol, max_iter, done));
+  if (rc) return rc;
+  return check_err(h);
+}
+
+int cmcg_slot_take(cmcg_handle* h, int slot, double* e_re, double* e_im, double* h_re, double* h_im,
+                   cmcg_info* info) {
+  if (!h || h->coupled || slot < 0 || slot >= h->nprob) return CMCG_ERR_INVALID_ARG;
+  if (h->slot_phase.empty() || h->slot_phase[size_t(slot)] != SLOT_DONE) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  const Prob& P = h->P[size_t(slot)];
+  const size_t half = size_t(h->nt_total) * 3 * h->np;
+  const size_t off = size_t(P.ext0) * 3 * h->np, cnt = size_t(P.nt) * 3 * h->np;
+  if (e_re) CK(cudaMemcpyAsync(e_re, h->ext0 + off, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (e_im) CK(cudaMemcpyAsync(e_im, h->ext0 + half + off, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (h_re) CK(cudaMemcpyAsync(h_re, h->ext1 + off, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (h_im) CK(cudaMemcpyAsync(h_im, h->ext1 + half + off, cnt * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const cmcg_info& I = h->slot_info[size_t(slot)];
+  if (info) *info = I;
+  h->slot_phase[size_t(slot)] = SLOT_EMPTY;
+  return I.status;
+}
 
 int cmcg_solve_multifreq(cmcg_handle* h, int nharm, const int* harmonics, const double* const* j_re,
                          const double* const* j_im, double tol, int max_iter, double* const* e_re,

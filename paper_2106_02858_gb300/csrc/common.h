@@ -205,6 +205,11 @@ void launch_to_external(const R* in, int ncomp_in, int c_in0, double* ext, int n
 template <typename R>
 void launch_lincomb3(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n, cudaStream_t s);
 
+// The same on the tiles of the problems with mask[p] != 0 only (tprob: problem of each tile, or null).
+template <typename R>
+void launch_lincomb3_masked(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n, int np,
+                            const int32_t* tprob, const int32_t* mask, cudaStream_t s);
+
 // (eps, mu)-weighted dots and CG updates, one partial per block of the table.
 template <typename R>
 void launch_cg_after_adjoint(int q, const R* Uw, const R* WT, R* A, const R* D, const double* wdot, double* partials,
@@ -240,6 +245,7 @@ void launch_cg_direction(R* D, R* Uw, const R* Rv, const Scalars* sc, const int3
 //   which 1: dA = total, alpha = rr / dA (breakdown if dA <= 0)
 //   which 2: beta = total / rr, rr = total, iters += 1, active = (sqrt(rr) > tol sqrt(rr0))
 //   which 3: rr_new = total
+//   which 4: as 0, for the problems with used[p] != 0 only (the others are left untouched)
 // Problems with pactive[p] == 0 are left alone for which 1 and 2.
 void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, int32_t* pactive, const int32_t* used,
                      int which, double tol, cudaStream_t s);

@@ -2,12 +2,13 @@
 //
 // A server owns registered models (a mesh with its materials, frequency and
 // order) and a queue of requests (one source each).  Worker threads, each with
-// its own CUDA stream, take the oldest queued request, gather up to the
-// model's batch capacity of queued requests of the same model (waiting at
-// most max_wait_ms for more), and solve them together with
-// cmcg_solve_batch_n on a pooled batch handle.  Requests that arrive while
-// other batches are on the GPU are admitted as soon as a worker and a handle
-// are free; several batches run concurrently on different streams.  Handles
+// its own CUDA stream, take the model of the oldest queued request, wait at
+// most max_wait_ms for more of that model, and run a pooled batch handle of it
+// as slots (cmcg_slot_*): every round advances each busy slot by one step of its
+// solve, and between rounds requests of that model that have arrived meanwhile
+// take the slots that finished requests left free, while the other slots keep
+// iterating.  The worker keeps the handle while it has busy slots or queued
+// requests of its model; several handles run concurrently on different streams.  Handles
 // are created lazily and kept (no cudaFree while serving); a new handle is
 // created only if the server's device-memory total stays within the HBM
 // budget, otherwise the batch waits for a pooled handle to come back.  All
@@ -106,26 +107,18 @@ void worker_main(cmcg_server* s) {
       continue;
     }
     Request* first = s->queue.front();
-    Model& m = *s->models[first->model];
-    // Micro-batching window: wait for more requests of this model, up to its capacity.
+    const int mid = first->model;
+    Model& m = *s->models[mid];
+    // Micro-batching window before the first round: wait for more requests of this model.
     auto count = [&] {
       int c = 0;
       for (Request* r : s->queue)
-        if (r->model == first->model) ++c;
+        if (r->model == mid) ++c;
       return c;
     };
     const auto deadline = first->t_submit + window;
     while (!s->stop && count() < m.capacity && Clock::now() < deadline) s->cv_work.wait_until(lk, deadline);
     if (s->queue.empty() || s->queue.front() != first) continue;  // another worker took it
-    std::vector<Request*> batch;
-    for (auto it = s->queue.begin(); it != s->queue.end() && int(batch.size()) < m.capacity;) {
-      if ((*it)->model == first->model) {
-        batch.push_back(*it);
-        it = s->queue.erase(it);
-      } else {
-        ++it;
-      }
-    }
     // A handle: pooled, or new within the HBM budget, or wait for one to come back.
     cmcg_handle* h = nullptr;
     int rc = CMCG_OK;
@@ -156,50 +149,102 @@ void worker_main(cmcg_server* s) {
       }
       s->cv_handle.wait(lk);
     }
-    const auto t_start = Clock::now();
-    for (Request* r : batch) r->t_start = t_start;
-    if (rc == CMCG_OK) {
+    if (rc != CMCG_OK) {  // the oldest request of this model fails; the others wait for a handle
+      for (auto it = s->queue.begin(); it != s->queue.end(); ++it)
+        if (*it == first) {
+          s->queue.erase(it);
+          break;
+        }
+      first->status = rc;
+      first->t_start = first->t_end = Clock::now();
+      first->done = true;
+      s->completed++;
+      s->cv_done.notify_all();
+      continue;
+    }
+    cmcg_set_stream(h, stream);
+    // Slot loop: requests of this model are admitted into free slots between rounds while the
+    // others iterate; each round advances every busy slot (cmcg_slot_round).
+    std::vector<Request*> slot(size_t(m.capacity), nullptr);
+    int busy = 0;
+    bool broken = false;
+    for (;;) {
+      std::vector<int> admit;
+      for (int sl = 0; sl < m.capacity; ++sl) {
+        if (slot[size_t(sl)]) continue;
+        auto it = s->queue.begin();
+        while (it != s->queue.end() && (*it)->model != mid) ++it;
+        if (it == s->queue.end()) break;
+        Request* r = *it;
+        s->queue.erase(it);
+        r->t_start = Clock::now();
+        slot[size_t(sl)] = r;
+        admit.push_back(sl);
+        ++busy;
+      }
+      if (busy == 0) break;
       lk.unlock();
-      const int n = int(batch.size());
-      std::vector<const double*> jr(n), ji(n);
-      std::vector<double*> er(n), ei(n), hr(n), hi(n);
-      for (int i = 0; i < n; ++i) {
-        Request* r = batch[i];
-        jr[i] = r->jre.data();
-        ji[i] = r->has_im ? r->jim.data() : nullptr;
-        const size_t len = size_t(m.nt) * 3 * m.np;
-        r->ere.resize(len);
-        r->eim.resize(len);
-        r->hre.resize(len);
-        r->him.resize(len);
-        er[i] = r->ere.data();
-        ei[i] = r->eim.data();
-        hr[i] = r->hre.data();
-        hi[i] = r->him.data();
+      std::vector<std::pair<int, int>> failed;  // (slot, status)
+      for (int sl : admit) {
+        Request* r = slot[size_t(sl)];
+        const int arc = cmcg_slot_admit(h, sl, r->jre.data(), r->has_im ? r->jim.data() : nullptr);
+        if (arc) failed.emplace_back(sl, arc);
       }
-      std::vector<cmcg_info> infos(n);
-      cmcg_set_stream(h, stream);
-      rc = cmcg_solve_batch_n(h, n, jr.data(), ji.data(), s->opt.tol, s->opt.max_iter, er.data(), ei.data(),
-                              hr.data(), hi.data(), infos.data());
+      std::vector<int> done(size_t(m.capacity), 0);
+      int rrc = failed.size() == admit.size() && !admit.empty() && busy == int(admit.size())
+                    ? CMCG_OK
+                    : cmcg_slot_round(h, s->opt.tol, s->opt.max_iter, done.data());
+      std::vector<std::pair<int, int>> finished;  // (slot, status)
+      if (rrc == CMCG_OK) {
+        for (int sl = 0; sl < m.capacity; ++sl) {
+          if (!done[size_t(sl)]) continue;
+          Request* r = slot[size_t(sl)];
+          const size_t len = size_t(m.nt) * 3 * m.np;
+          r->ere.resize(len);
+          r->eim.resize(len);
+          r->hre.resize(len);
+          r->him.resize(len);
+          const int st = cmcg_slot_take(h, sl, r->ere.data(), r->eim.data(), r->hre.data(), r->him.data(), &r->info);
+          finished.emplace_back(sl, st);
+        }
+      }
       lk.lock();
-      for (int i = 0; i < n; ++i) {
-        batch[i]->info = infos[i];
-        batch[i]->status = rc < 0 ? rc : infos[i].status;
+      auto complete = [&](int sl, int st) {
+        Request* r = slot[size_t(sl)];
+        if (!r) return;
+        r->status = st;
+        r->t_end = Clock::now();
+        r->done = true;
+        r->jre.clear();
+        r->jim.clear();
+        slot[size_t(sl)] = nullptr;
+        --busy;
+        s->completed++;
+      };
+      for (auto& f : failed) complete(f.first, f.second);
+      for (auto& f : finished) complete(f.first, f.second);
+      if (rrc != CMCG_OK) {  // the handle's state is unknown: fail what it holds and drop it
+        for (int sl = 0; sl < m.capacity; ++sl) complete(sl, rrc);
+        broken = true;
       }
-      m.idle.push_back(h);
-      s->cv_handle.notify_all();
+      if (!failed.empty() || !finished.empty() || broken) s->cv_done.notify_all();
+      if (broken) break;
+    }
+    if (broken) {
+      s->bytes_in_use -= cmcg_device_bytes(h);
+      s->nhandles--;
+      for (auto it = s->all_handles.begin(); it != s->all_handles.end(); ++it)
+        if (*it == h) {
+          s->all_handles.erase(it);
+          break;
+        }
+      lk.unlock();
+      cmcg_destroy(h);
+      lk.lock();
     } else {
-      for (Request* r : batch) r->status = rc;
+      m.idle.push_back(h);
     }
-    const auto t_end = Clock::now();
-    for (Request* r : batch) {
-      r->t_end = t_end;
-      r->done = true;
-      r->jre.clear();
-      r->jim.clear();
-    }
-    s->completed += int64_t(batch.size());
-    s->cv_done.notify_all();
+    s->cv_handle.notify_all();
   }
   lk.unlock();
   cudaStreamDestroy(stream);

@@ -64,6 +64,22 @@ __global__ void to_external_kernel(const R* __restrict__ in, int ncomp_in, int c
   }
 }
 
+// o = a x + b y on the tiles of the problems with mask[p] != 0 (problem of tile t: tprob[t], or 0).
+template <typename R>
+__global__ void lincomb_masked_kernel(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n,
+                                      int64_t tile_len, const int32_t* tprob, const int32_t* mask) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int p = tprob ? tprob[i / tile_len] : 0;
+    if (!mask[p]) continue;
+    double v = a * double(x[i]);
+    if (y) v += b * double(y[i]);
+    const R r = R(v);
+    if (o1) o1[i] = r;
+    if (o2) o2[i] = r;
+    if (o3) o3[i] = r;
+  }
+}
+
 template <typename R>
 __global__ void lincomb_kernel(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -298,6 +314,15 @@ __global__ void finalize_kernel(const double* partials, const BlockTable bt, Sca
     S.rr_new = tot;
     return;
   }
+  if (which == 4) {  // as 0, for the problems of `used` only (the others are left untouched)
+    if (!used || !used[p]) return;
+    S.rr = tot;
+    S.rr0 = tot;
+    S.iters = 0;
+    S.status = isfinite(tot) ? 0 : CMCG_ERR_NONFINITE;
+    if (pactive) pactive[p] = (S.status == 0 && tot > 0 && sqrt(tot) > tol * sqrt(tot)) ? 1 : 0;
+    return;
+  }
   if (which == 0) {
     S.rr = tot;
     S.rr0 = tot;
@@ -370,6 +395,12 @@ void launch_to_external(const R* in, int ncomp_in, int c_in0, double* ext, int n
                                                          np);
 }
 template <typename R>
+void launch_lincomb3_masked(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n, int np,
+                            const int32_t* tprob, const int32_t* mask, cudaStream_t s) {
+  lincomb_masked_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(o1, o2, o3, a, x, b, y, n, int64_t(6) * np * TILE, tprob,
+                                                            mask);
+}
+template <typename R>
 void launch_lincomb3(R* o1, R* o2, R* o3, double a, const R* x, double b, const R* y, int64_t n, cudaStream_t s) {
   lincomb_kernel<R><<<grid_for(n, 256), 256, 0, s>>>(o1, o2, o3, a, x, b, y, n);
 }
@@ -434,6 +465,8 @@ void launch_finalize(const double* partials, const BlockTable& bt, Scalars* sc, 
   template void launch_to_external<R>(const R*, int, int, double*, int, int, int, const int32_t*, int64_t, int,       \
                                       cudaStream_t);                                                                  \
   template void launch_lincomb3<R>(R*, R*, R*, double, const R*, double, const R*, int64_t, cudaStream_t);             \
+  template void launch_lincomb3_masked<R>(R*, R*, R*, double, const R*, double, const R*, int64_t, int,                 \
+                                          const int32_t*, const int32_t*, cudaStream_t);                                \
   template void launch_cg_after_adjoint<R>(int, const R*, const R*, R*, const R*, const double*, double*,              \
                                            const BlockTable&, const int32_t*, cudaStream_t);                          \
   template void launch_cg_update<R>(int, R*, R*, const R*, const R*, const double*, const Scalars*, double*,          \

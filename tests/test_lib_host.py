@@ -173,6 +173,10 @@ def test_every_handle_entry_rejects_a_null_handle(lib):
         "cmcg_fw_solve_batch": lambda: L.cmcg_fw_solve_batch(None, 2, pp, None, pp, pp, pp, pp),
         "cmcg_set_boundary_data": lambda: L.cmcg_set_boundary_data(None, 0, p, None),
         "cmcg_set_conductivity": lambda: L.cmcg_set_conductivity(None, 0, p),
+        "cmcg_slot_admit": lambda: L.cmcg_slot_admit(None, 0, p, None),
+        "cmcg_slot_round": lambda: L.cmcg_slot_round(None, 1e-6, 10, None),
+        "cmcg_slot_take": lambda: L.cmcg_slot_take(None, 0, p, p, p, p, None),
+        "cmcg_slot_state": lambda: L.cmcg_slot_state(None, 0),
         "cmcg_solve_multifreq": lambda: L.cmcg_solve_multifreq(None, 1, (C.c_int * 1)(1), pp, None, 1e-6, 10, pp, pp,
                                                                pp, pp, None),
         "cmcg_measure_peaks": lambda: L.cmcg_measure_peaks(-1, None, None),
