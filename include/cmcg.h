@@ -401,6 +401,19 @@ int cmcg_slot_round(cmcg_handle* h, double tol, int max_iter, int* done);
 int cmcg_slot_take(cmcg_handle* h, int slot, double* e_re, double* e_im, double* h_re, double* h_im, cmcg_info* info);
 int cmcg_slot_state(const cmcg_handle* h, int slot);
 
+/* Checkpoint / resume of a slot between rounds (the paper has no counterpart).
+ * cmcg_slot_save writes the state of an admitted, iterating or filter-pending
+ * slot -- its CG state U0, R, D, the FP64 CG scalars, and its source -- into
+ * buf (at least cmcg_slot_state_bytes(h, slot) bytes, host memory) and empties
+ * the slot.  cmcg_slot_restore puts such a state into an empty slot of any
+ * handle whose problem in that slot has the same mesh size, order, precision,
+ * M, dt and omega (else CMCG_ERR_INVALID_ARG); the request then continues as
+ * if it had never stopped (the same bits).  The state is in the handle's
+ * internal layout and precision, for the same library build. */
+int64_t cmcg_slot_state_bytes(const cmcg_handle* h, int slot);
+int cmcg_slot_save(cmcg_handle* h, int slot, void* buf, int64_t len);
+int cmcg_slot_restore(cmcg_handle* h, int slot, const void* buf, int64_t len);
+
 /* Device memory held by a handle, in bytes (the figure cmcg_create checks
  * against hbm_budget_bytes). */
 int64_t cmcg_device_bytes(const cmcg_handle* h);

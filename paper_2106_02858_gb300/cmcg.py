@@ -136,6 +136,9 @@ def _load() -> C.CDLL:
         "cmcg_slot_round": (C.c_int, [_vp, C.c_double, C.c_int, C.POINTER(C.c_int)]),
         "cmcg_slot_take": (C.c_int, [_vp, C.c_int, _dp, _dp, _dp, _dp, C.POINTER(cmcg_info)]),
         "cmcg_slot_state": (C.c_int, [_vp, C.c_int]),
+        "cmcg_slot_state_bytes": (C.c_int64, [_vp, C.c_int]),
+        "cmcg_slot_save": (C.c_int, [_vp, C.c_int, _vp, C.c_int64]),
+        "cmcg_slot_restore": (C.c_int, [_vp, C.c_int, _vp, C.c_int64]),
         "cmcg_solve_multifreq": (C.c_int, [_vp, C.c_int, C.POINTER(C.c_int), C.POINTER(_dp), C.POINTER(_dp),
                                            C.c_double, C.c_int, C.POINTER(_dp), C.POINTER(_dp), C.POINTER(_dp),
                                            C.POINTER(_dp), C.POINTER(cmcg_info)]),
@@ -165,7 +168,7 @@ EXPORTED = ("cmcg_default_options", "cmcg_status_string", "cmcg_validate", "cmcg
             "cmcg_server_submit", "cmcg_server_poll", "cmcg_server_stats", "cmcg_server_destroy",
             "cmcg_measure_peaks", "cmcg_set_conductivity", "cmcg_partition_slabs", "cmcg_shard_plan",
             "cmcg_create_sharded", "cmcg_solve_multifreq", "cmcg_slot_admit", "cmcg_slot_round", "cmcg_slot_take",
-            "cmcg_slot_state")
+            "cmcg_slot_state", "cmcg_slot_state_bytes", "cmcg_slot_save", "cmcg_slot_restore")
 CMCG_NOALLOC_MAX_TETS = 1048576
 
 
@@ -326,6 +329,21 @@ def cmcg_slot_take(h: Handle, slot: int):
 
 def cmcg_slot_state(h: Handle, slot: int) -> int:
     return int(_lib.cmcg_slot_state(h.ptr, int(slot)))
+
+
+def cmcg_slot_save(h: Handle, slot: int) -> bytes:
+    """Checkpoint of a busy slot (the slot becomes empty)."""
+    n = int(_lib.cmcg_slot_state_bytes(h.ptr, int(slot)))
+    if n < 0:
+        raise CMCGError(n, "cmcg_slot_state_bytes")
+    buf = C.create_string_buffer(n)
+    _check(_lib.cmcg_slot_save(h.ptr, int(slot), buf, n), "cmcg_slot_save")
+    return buf.raw
+
+
+def cmcg_slot_restore(h: Handle, slot: int, state: bytes) -> None:
+    buf = C.create_string_buffer(state, len(state))
+    _check(_lib.cmcg_slot_restore(h.ptr, int(slot), buf, len(state)), "cmcg_slot_restore")
 
 
 def cmcg_solve_multifreq(h: Handle, harmonics, j_re, j_im=None, tol: float = 1e-8, max_iter: int = 1000):

@@ -33,9 +33,22 @@
 #include <new>
 #include <tuple>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.h"
 
 using namespace cmcg;
+
+namespace {
+// NVTX range for the lifetime of a scope (host side: sweeps, solve phases, slot rounds); free
+// when no profiling tool is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
+}  // namespace
 
 namespace {
 
@@ -402,6 +415,7 @@ void prof_collect(cmcg_handle* h) {
 // sign.  pactive: skip problems whose CG has stopped (nullptr: sweep all).
 template <typename R>
 void sweep_free(cmcg_handle* h, bool adjoint, const int32_t* pactive) {
+  Range rg(adjoint ? "cmcg: adjoint sweep" : "cmcg: forward sweep");
   cmcg_handle::SweepEv* pe = prof_begin(h, false);
   R* Uw = (R*)h->Uw;
   R* vA = (R*)h->vA;
@@ -428,6 +442,7 @@ void sweep_free(cmcg_handle* h, bool adjoint, const int32_t* pactive) {
 // on-the-fly filter (one extra launch evaluates Phi at t_M).
 template <typename R>
 void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* mask = nullptr) {
+  Range rg(filter ? "cmcg: filtered source sweep" : "cmcg: source sweep");
   cmcg_handle::SweepEv* pe = prof_begin(h, true);
   R* Uw = (R*)h->Uw;
   R* vA = (R*)h->vA;
@@ -763,6 +778,7 @@ int solve_dev(cmcg_handle* h, int nused, const double* const* j_re, const double
 // of `mask` (nullptr: all); U0 holds the result.
 template <typename R>
 int cg_phase(cmcg_handle* h, const int32_t* mask, double tol, int max_iter) {
+  Range rg("cmcg: init and CG");
   int rc = CMCG_OK;
   CK(cudaMemsetAsync(h->sc, 0, sizeof(Scalars) * h->nprob, h->stream));
   // Algorithm init: G = P_psi 0, G_T = P* G, G* = G - G_T.
@@ -784,6 +800,7 @@ int cg_phase(cmcg_handle* h, const int32_t* mask, double tol, int max_iter) {
   };
   int it = 0;
   while (any_active() && it < max_iter) {
+    Range rit("cmcg: CG iteration");
     // Algorithm grad on D: W_T = P D - D; A = P* W_T - W_T.
     sweep_free<R>(h, false, h->pactive);
     lincomb<R>(h, h->WT, h->Uw, nullptr, 1.0, h->Uw, -1.0, h->D);
@@ -968,6 +985,7 @@ void zero_tiles(cmcg_handle* h, void* v, int p) {
 
 template <typename R>
 int slot_round_dev(cmcg_handle* h, double tol, int max_iter, int* done) {
+  Range rg("cmcg: slot round");
   const int n = h->nprob;
   int32_t* mh = h->slot_masks_host;  // [admitted | adjoint | final]
   int32_t* m_init = h->slot_masks;
@@ -2000,6 +2018,112 @@ int cmcg_slot_take(cmcg_handle* h, int slot, double* e_re, double* e_im, double*
   if (info) *info = I;
   h->slot_phase[size_t(slot)] = SLOT_EMPTY;
   return I.status;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Saved state of a slot (checkpoint between rounds): a header, then the problem's tiles of U0, R,
+// D (6 Np values per tetrahedron each) and of the source J_re, J_im (3 Np each), in the handle's
+// precision and internal layout.  Between rounds Uw holds D for an iterating slot; A and W_T are
+// scratch of a round.  Restoring it gives the same bits as never having stopped.
+struct SlotHeader {
+  char magic[8];
+  int32_t prec, q, np, M, phase, pactive;
+  int64_t nt, ntiles;
+  double dt, omega;
+  Scalars sc;
+};
+constexpr char SLOT_MAGIC[8] = {'C', 'M', 'C', 'G', 'S', 'L', 'T', '1'};
+
+size_t slot_payload(const cmcg_handle* h, int slot) {
+  const Prob& P = h->P[size_t(slot)];
+  return size_t(P.ntiles) * TILE * h->np * h->rsize * (3 * 6 + 2 * 3);
+}
+
+}  // namespace
+
+extern "C" {
+
+int64_t cmcg_slot_state_bytes(const cmcg_handle* h, int slot) {
+  if (!h || h->coupled || slot < 0 || slot >= h->nprob) return CMCG_ERR_INVALID_ARG;
+  return int64_t(sizeof(SlotHeader) + slot_payload(h, slot));
+}
+
+int cmcg_slot_save(cmcg_handle* h, int slot, void* buf, int64_t len) {
+  if (!h || h->coupled || slot < 0 || slot >= h->nprob || !buf || len < cmcg_slot_state_bytes(h, slot))
+    return CMCG_ERR_INVALID_ARG;
+  if (h->slot_phase.empty()) return CMCG_ERR_INVALID_ARG;
+  const int ph = h->slot_phase[size_t(slot)];
+  if (ph != SLOT_ADMITTED && ph != SLOT_CG && ph != SLOT_FINAL) return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  const Prob& P = h->P[size_t(slot)];
+  SlotHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, SLOT_MAGIC, 8);
+  hd.prec = h->prec;
+  hd.q = h->q;
+  hd.np = h->np;
+  hd.M = P.M;
+  hd.phase = ph;
+  hd.nt = P.nt;
+  hd.ntiles = P.ntiles;
+  hd.dt = P.dt;
+  hd.omega = P.omega;
+  CK(cudaMemcpyAsync(&hd.sc, h->sc + slot, sizeof(Scalars), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&hd.pactive, h->pactive + slot, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+  char* out = static_cast<char*>(buf) + sizeof(SlotHeader);
+  const size_t v6 = size_t(P.ntiles) * 6 * h->np * TILE * h->rsize, v3 = v6 / 2;
+  const size_t o6 = size_t(P.tile0) * 6 * h->np * TILE * h->rsize, o3 = o6 / 2;
+  const void* src6[3] = {h->U0, h->Rv, h->D};
+  for (int k = 0; k < 3; ++k, out += v6)
+    CK(cudaMemcpyAsync(out, static_cast<const char*>(src6[k]) + o6, v6, cudaMemcpyDeviceToHost, h->stream));
+  const void* src3[2] = {h->Jre, h->Jim};
+  for (int k = 0; k < 2; ++k, out += v3)
+    CK(cudaMemcpyAsync(out, static_cast<const char*>(src3[k]) + o3, v3, cudaMemcpyDeviceToHost, h->stream));
+  const int32_t zero = 0;
+  CK(cudaMemcpyAsync(h->pactive + slot, &zero, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(buf, &hd, sizeof(hd));
+  h->pactive_host[slot] = 0;
+  h->slot_phase[size_t(slot)] = SLOT_EMPTY;
+  return CMCG_OK;
+}
+
+int cmcg_slot_restore(cmcg_handle* h, int slot, const void* buf, int64_t len) {
+  if (!h || h->coupled || slot < 0 || slot >= h->nprob || !buf || len < int64_t(sizeof(SlotHeader)))
+    return CMCG_ERR_INVALID_ARG;
+  SlotHeader hd;
+  std::memcpy(&hd, buf, sizeof(hd));
+  const Prob& P = h->P[size_t(slot)];
+  if (std::memcmp(hd.magic, SLOT_MAGIC, 8) != 0 || hd.prec != h->prec || hd.q != h->q || hd.np != h->np ||
+      hd.M != P.M || hd.nt != P.nt || hd.ntiles != P.ntiles || hd.dt != P.dt || hd.omega != P.omega ||
+      (hd.phase != SLOT_ADMITTED && hd.phase != SLOT_CG && hd.phase != SLOT_FINAL) ||
+      len < int64_t(sizeof(SlotHeader) + slot_payload(h, slot)))
+    return CMCG_ERR_INVALID_ARG;
+  if (cudaSetDevice(h->device) != cudaSuccess) return CMCG_ERR_CUDA;
+  int rc = slot_setup(h);
+  if (rc) return rc;
+  if (h->slot_phase[size_t(slot)] != SLOT_EMPTY) return CMCG_ERR_INVALID_ARG;
+  const char* in = static_cast<const char*>(buf) + sizeof(SlotHeader);
+  const size_t v6 = size_t(P.ntiles) * 6 * h->np * TILE * h->rsize, v3 = v6 / 2;
+  const size_t o6 = size_t(P.tile0) * 6 * h->np * TILE * h->rsize, o3 = o6 / 2;
+  void* dst6[3] = {h->U0, h->Rv, h->D};
+  for (int k = 0; k < 3; ++k, in += v6)
+    CK(cudaMemcpyAsync(static_cast<char*>(dst6[k]) + o6, in, v6, cudaMemcpyHostToDevice, h->stream));
+  void* dst3[2] = {h->Jre, h->Jim};
+  for (int k = 0; k < 2; ++k, in += v3)
+    CK(cudaMemcpyAsync(static_cast<char*>(dst3[k]) + o3, in, v3, cudaMemcpyHostToDevice, h->stream));
+  // an iterating slot starts its next round with Uw = D
+  CK(cudaMemcpyAsync(static_cast<char*>(h->Uw) + o6, static_cast<const char*>(h->D) + o6, v6,
+                     cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->sc + slot, &hd.sc, sizeof(Scalars), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->pactive + slot, &hd.pactive, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  h->pactive_host[slot] = hd.pactive;
+  h->slot_phase[size_t(slot)] = hd.phase;
+  return CMCG_OK;
 }
 
 int cmcg_solve_multifreq(cmcg_handle* h, int nharm, const int* harmonics, const double* const* j_re,

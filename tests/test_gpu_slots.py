@@ -84,3 +84,45 @@ def test_slot_state_machine_rejects_misuse(lib):
     lib.cmcg_slot_round(h, 1e-6, 100)
     assert lib.cmcg_slot_state(h, 0) == 2
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_checkpoint_and_resume_in_another_handle(lib, prec):
+    """A request saved mid-solve (after a few CG iterations), restored into another slot of
+    another handle of the same model and finished there, gives the bits of an uninterrupted solve;
+    a state of another model is rejected."""
+    b = I.batched_rhs(nrhs=2, n=3, order=2, tol=1e-6)
+    P = lib.CMCG_FP32 if prec == "fp32" else lib.CMCG_FP64
+    mesh = lib.make_mesh(b.mesh.verts, b.mesh.tets, b.mesh.tags)
+    opt = lib.cmcg_default_options(order=2, precision=P, stage_variant=2 if prec == "fp32" else 1)
+    h1 = lib.cmcg_create_batch([(mesh, b.eps, b.mu, b.omega)] * 2, opt)
+    h2 = lib.cmcg_create_batch([(mesh, b.eps, b.mu, b.omega)] * 3, opt)
+
+    def finish(h, slot):
+        for _ in range(2000):
+            if slot in lib.cmcg_slot_round(h, 1e-6, 400):
+                return lib.cmcg_slot_take(h, slot)
+        raise AssertionError("no result")
+
+    lib.cmcg_slot_admit(h1, 0, b.j_re[0], b.j_im[0])
+    ref = finish(h1, 0)
+    lib.cmcg_slot_admit(h1, 1, b.j_re[0], b.j_im[0])
+    for _ in range(5):
+        lib.cmcg_slot_round(h1, 1e-6, 400)
+    assert lib.cmcg_slot_state(h1, 1) == 2
+    state = lib.cmcg_slot_save(h1, 1)
+    assert lib.cmcg_slot_state(h1, 1) == 0
+    lib.cmcg_slot_admit(h2, 0, b.j_re[1], b.j_im[1])  # other work in the target handle
+    lib.cmcg_slot_round(h2, 1e-6, 400)
+    lib.cmcg_slot_restore(h2, 2, state)
+    assert lib.cmcg_slot_state(h2, 2) == 2
+    got = finish(h2, 2)
+    assert got[2].iters == ref[2].iters
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+    other = I.batched_rhs(nrhs=1, n=2, order=2)
+    m2 = lib.make_mesh(other.mesh.verts, other.mesh.tets, other.mesh.tags)
+    h3 = lib.cmcg_create_batch([(m2, other.eps, other.mu, other.omega)], opt)
+    with pytest.raises(lib.CMCGError):
+        lib.cmcg_slot_restore(h3, 0, state)
+    for h in (h1, h2, h3):
+        h.close()

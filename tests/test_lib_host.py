@@ -177,6 +177,9 @@ def test_every_handle_entry_rejects_a_null_handle(lib):
         "cmcg_slot_round": lambda: L.cmcg_slot_round(None, 1e-6, 10, None),
         "cmcg_slot_take": lambda: L.cmcg_slot_take(None, 0, p, p, p, p, None),
         "cmcg_slot_state": lambda: L.cmcg_slot_state(None, 0),
+        "cmcg_slot_state_bytes": lambda: L.cmcg_slot_state_bytes(None, 0),
+        "cmcg_slot_save": lambda: L.cmcg_slot_save(None, 0, p, 8),
+        "cmcg_slot_restore": lambda: L.cmcg_slot_restore(None, 0, p, 8),
         "cmcg_solve_multifreq": lambda: L.cmcg_solve_multifreq(None, 1, (C.c_int * 1)(1), pp, None, 1e-6, 10, pp, pp,
                                                                pp, pp, None),
         "cmcg_measure_peaks": lambda: L.cmcg_measure_peaks(-1, None, None),
