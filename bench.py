@@ -46,7 +46,7 @@ STAGE_SRC = os.path.join(ROOT, "paper_2106_02858_gb300", "csrc", "dg_stage.cuh")
 # FP32 stage-kernel forms, indexed by cmcg_options.stage_variant - 1.
 STAGE_FORMS = ["dg_stage_kernel<float, 1>", "dg_stage_kernel<float, 3>", "dg_stage_kernel<float, 4>",
                "dg_stage_quad<float, 4>", "dg_stage_quad<float, 5>", "dg_stage_quad<float, 6>",
-               "dg_stage_tc (tcgen05 3xTF32, 2 threads / tet)", "dg_stage_tc4 (tcgen05 3xTF32, 4 threads / tet)"]
+               "dg_stage_tc (tcgen05 3xTF32)"]
 
 
 def peaks():

@@ -133,11 +133,10 @@ typedef struct cmcg_mesh {
  *                     FP32: 0, 1, 2 = two threads per tetrahedron (E / H)
  *                     with at least 1, 3, 4 resident 128-thread blocks per
  *                     SM; 3, 4, 5 = four threads per tetrahedron (E / H x
- *                     node half) with at least 4, 5, 6; 6, 7 = the volume
- *                     and lift contractions on the tensor cores (tcgen05,
- *                     three TF32 products per FP32 product, FP32
- *                     accumulation) with two / four threads per
- *                     tetrahedron.  FP64: 0 = two threads
+ *                     node half) with at least 4, 5, 6; 6 = the volume and
+ *                     lift contractions on the tensor cores (tcgen05, three
+ *                     TF32 products per FP32 product, FP32 accumulation),
+ *                     two threads per tetrahedron.  FP64: 0 = two threads
  *                     per tetrahedron; 1, 2 = four threads with at least
  *                     2, 3.  Other k: CMCG_ERR_INVALID_ARG.  Results do not
  *                     depend on it beyond rounding.
@@ -275,9 +274,9 @@ int cmcg_set_stream(cmcg_handle* h, void* stream);
 
 /* Stage-kernel form in use (0-based, as stage_variant - 1) and, when it was
  * chosen by timing at creation, the measured microseconds per stage of each
- * form (10 entries: [0..7] indexed by form, see stage_variant; [8] the chosen
- * form with stage_overlap on; [9] unused; -1 where not timed or rejected by the
- * device).  Any pointer may be NULL. */
+ * form (10 entries: [0..6] indexed by form, see stage_variant; [7] the chosen
+ * form with stage_overlap on; [8], [9] unused; -1 where not timed or rejected by
+ * the device).  Any pointer may be NULL. */
 int cmcg_get_tuning(const cmcg_handle* h, int* variant, double* us_per_stage);
 
 /* Sizes of the handle: nt, Np, M (steps per period), dt, number of doubles of

@@ -146,7 +146,7 @@ struct cmcg_handle {
   std::map<std::tuple<int, const void*, bool>, cudaGraphExec_t> graph_exec;
   int form = 0;      // stage-kernel form (see launch_stage)
   bool pdl = false;  // stages launched with programmatic stream serialisation
-  double tune_us[10];     // [0..7] per form, [8] the chosen form with overlapped launches, [9] unused
+  double tune_us[10];     // [0..6] per form, [7] the chosen form with overlapped launches, [8..9] unused
   int32_t* err = nullptr;       // device status word of the stage kernels' bounded waits
   int32_t* err_host = nullptr;  // pinned
   // sweep profiling
@@ -562,7 +562,7 @@ int autotune(cmcg_handle* h, int nforms, int overlap) {
     double us;
     int rc = time_one(&us);
     if (rc) return rc;
-    h->tune_us[8] = us;
+    h->tune_us[7] = us;
     h->pdl = us >= 0 && us < best;
   } else {
     h->pdl = overlap == 1;

@@ -155,14 +155,13 @@ struct StageArgs {
 // Kernel launchers, one translation unit per order.
 // form: stage-kernel form.  FP32: 0, 1, 2 = two threads per tetrahedron with at
 // least 1, 3, 4 resident 128-thread blocks per SM; 3, 4, 5 = four threads per
-// tetrahedron with at least 4, 5, 6; 6, 7 = tensor-core contractions (tcgen05,
-// 3xTF32) with two / four threads per tetrahedron.  FP64: 0 = two threads per
+// tetrahedron with at least 4, 5, 6; 6 = tensor-core contractions (tcgen05,
+// 3xTF32) with two threads per tetrahedron.  FP64: 0 = two threads per
 // tetrahedron, 1, 2 = four threads per tetrahedron with at least 2, 3 blocks.
 // pdl: launch with programmatic stream serialisation (the stage overlaps the
 // previous stage's tail).
-constexpr int STAGE_FORMS_F32 = 8;
+constexpr int STAGE_FORMS_F32 = 7;
 constexpr int STAGE_FORM_TC = 6;
-constexpr int STAGE_FORM_TC4 = 7;
 constexpr int STAGE_FORMS_F64 = 3;
 template <int Q, typename R>
 void launch_stage(const StageArgs<R>& a, cudaStream_t s, int form, bool pdl);

@@ -647,10 +647,6 @@ void launch_stage<CMCG_Q, float>(const StageArgs<float>& a, cudaStream_t s, int 
       launch_k(dg_stage_tc<TC_MINB>, unsigned((a.nti + TC_TETS - 1) / TC_TETS), TC_THREADS,
                tc_smem(a.acc_out != nullptr), s, pdl, a);
       break;
-    case STAGE_FORM_TC4:
-      launch_k(dg_stage_tc4<TC_MINB>, unsigned((a.nti + TC_TETS - 1) / TC_TETS), T4_THREADS,
-               tc4_smem(a.acc_out != nullptr), s, pdl, a);
-      break;
     default: launch_k(dg_stage_kernel<float, 1>, blocks, STAGE_THREADS, sm, s, pdl, a); break;
   }
 }
@@ -679,7 +675,6 @@ void upload_constants<CMCG_Q>(const RefMats& rm) {
   cudaFuncSetAttribute(dg_stage_quad<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<double>()));
   cudaFuncSetAttribute(dg_stage_quad<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<double>()));
   cudaFuncSetAttribute(dg_stage_tc<TC_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc_smem(true)));
-  cudaFuncSetAttribute(dg_stage_tc4<TC_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc4_smem(true)));
   tc_upload_reference(rm);
   const int np = rm.np, nfp = rm.nfp;
   std::vector<double> D(3 * np * np);

@@ -22,10 +22,10 @@
 // derivatives read back from TMEM, on the CUDA cores.
 //
 // Precision (3xTF32).  Every FP32 value x is split x = hi + lo with hi = x
-// rounded to TF32 (10 explicit mantissa bits) and lo = (x - hi) rounded to TF32;
-// a product is hi_a hi_b + lo_a hi_b + hi_a lo_b (the lo_a lo_b term, ~2^-22
-// relative, is dropped), accumulated in FP32 in TMEM.  The reference matrices are
-// split on the host from double.
+// rounded to TF32 (10 explicit mantissa bits) and lo = x - hi, of which the tensor
+// core reads the leading TF32 bits; a product is hi_a hi_b + lo_a hi_b + hi_a lo_b
+// (the lo_a lo_b term, ~2^-22 relative, is dropped), accumulated in FP32 in TMEM.
+// The reference matrices are split on the host from double (both parts rounded).
 //
 // Synchronisation.  One thread issues every MMA of the CTA and commits them to
 // an mbarrier; all waits on mbarriers are bounded (about one second of
@@ -38,9 +38,8 @@ constexpr int TC_THREADS = 128;
 constexpr int TC_TETS = 64;
 constexpr int TC_KV = (NPQ + 7) / 8 * 8;              // volume K (nodes), padded to the MMA K of 8
 constexpr int TC_KL = (4 * NFPQ + 7) / 8 * 8;         // lift K (face nodes f Nfp + jf)
-// Accumulator columns.  The output nodes are split in two halves of NH (the node ranges of
-// the two thread groups of dg_stage_tc4); each half's columns form one aligned block, so a
-// group reads its nodes with one or two wide TMEM loads:
+// Accumulator columns.  The output nodes are split in two halves of NH, each half's columns
+// one aligned block (a layout that lets a thread group own one node half):
 //   volume: column of (b, i) = h VBLK + b NH + (i - h NH), h = i / NH;   N = 2 VBLK
 //   lift:   column of i      = h LBLK + (i - h NH);                       N = 2 LBLK
 constexpr int TC_NH = NPQ / 2;
@@ -100,9 +99,11 @@ __host__ __device__ constexpr uint32_t tc_idesc(int m, int n) {
 
 // Round an FP32 bit pattern to TF32 (nearest, ties away from zero).
 __device__ __forceinline__ uint32_t tf32_rn(uint32_t u) { return (u + 0x1000u) & 0xFFFFE000u; }
+// x = hi + lo with hi = x rounded to TF32 and lo = x - hi exactly (|lo| <= 2^-11 |x|); the
+// tensor core reads lo's leading TF32 bits (it truncates), which keeps hi + lo within 2^-21 |x|.
 __device__ __forceinline__ void tf32_split(float x, uint32_t& hi, uint32_t& lo) {
   hi = tf32_rn(__float_as_uint(x));
-  lo = tf32_rn(__float_as_uint(x - __uint_as_float(hi)));
+  lo = __float_as_uint(x - __uint_as_float(hi));
 }
 
 __device__ __forceinline__ void tmem_st8(uint32_t addr, const uint32_t (&v)[8]) {
@@ -121,42 +122,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t addr, float (&f)[16]) {
       : "memory");
 #pragma unroll
   for (int k = 0; k < 16; ++k) f[k] = __uint_as_float(v[k]);
-}
-// N consecutive TMEM columns of this thread's lane (N = 8, 16 or 32, column aligned to N); the
-// wait for the load is part of the same asm statement, so the values are only used after it.
-template <int N>
-__device__ __forceinline__ void tmem_ld_block(uint32_t addr, float (&f)[N]);
-template <>
-__device__ __forceinline__ void tmem_ld_block<8>(uint32_t addr, float (&f)[8]) {
-  uint32_t v[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-      : "r"(addr)
-      : "memory");
-#pragma unroll
-  for (int k = 0; k < 8; ++k) f[k] = __uint_as_float(v[k]);
-}
-template <>
-__device__ __forceinline__ void tmem_ld_block<16>(uint32_t addr, float (&f)[16]) {
-  tmem_ld16(addr, f);
-}
-template <>
-__device__ __forceinline__ void tmem_ld_block<32>(uint32_t addr, float (&f)[32]) {
-  uint32_t v[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
-        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(addr)
-      : "memory");
-#pragma unroll
-  for (int k = 0; k < 32; ++k) f[k] = __uint_as_float(v[k]);
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
@@ -557,373 +522,6 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
         a.out[o] = bs[(c * NP + n) * TC_THREADS] + cf.c_out * phi[c][n];
       }
   }
-}
-
-// ------------------------------------------------------------------------------------------
-// Four threads per tetrahedron: the same MMAs with two thread groups of 128 per CTA sharing
-// each TMEM lane (row).  Group g = tid / 128 (warps 4g .. 4g + 3; warp w reaches TMEM lanes
-// 32 (w mod 4) ..) computes the fluxes of faces 2g, 2g + 1 and the output rows of the nodes
-// [g NH, g NH + NH); it writes every second chunk of each A operand.  The own field is staged
-// in shared memory, so the face loop is not unrolled and the face-node tables are read from
-// constant memory; each group reads its accumulator block with one wide TMEM load per
-// component.  Extra CTA barriers: the field and traces before the A writes, and all volume
-// reads before the lift A overwrites those columns.
-constexpr int T4_THREADS = 256;
-__constant__ FaceTab cFMt = make_fmask(CMCG_Q);
-
-template <int MINB>
-__global__ void __launch_bounds__(T4_THREADS, MINB) dg_stage_tc4(const StageArgs<float> a) {
-  using R = float;
-  constexpr int NP = NPQ, NFP = NFPQ, NH = TC_NH;
-  constexpr int VS = 6 * NP * TILE;
-  constexpr int RW = 128;  // rows per CTA (slot stride)
-  constexpr uint32_t IDV = tc_idesc(128, TC_NV), IDL = tc_idesc(128, TC_NL);
-  grid_dep_launch();
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int g = tid >> 7;    // thread group
-  const int r = tid & 127;   // MMA row, TMEM lane
-  const int64_t gt = (int64_t)blockIdx.x * TC_TETS + (r >> 1);
-  const int half = r & 1;  // 0: owns E, computes Phi_H;  1: owns H, computes Phi_E
-  const int64_t tile = gt >> 5;
-  const int lane = int(gt & 31);
-  const bool in_range = gt < a.nti;
-
-  __shared__ __align__(8) uint64_t bars[2];
-  __shared__ uint32_t tmem_base;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* sB = smem_raw;
-  R* fs = reinterpret_cast<R*>(smem_raw + TC_B_BYTES) + r;  // own field [3 Np][rows]
-  R* tr = fs + 3 * NP * RW;                                  // traces, then fluxes [4 Nfp 3][rows]
-  R* bs = tr + TRACE_SLOTS * RW;                             // base rows [3 Np][rows]
-  R* acc_s = bs + 3 * NP * RW;                               // accumulator rows (source stages)
-
-  int prob = 0;
-  StageCoef<R> cf;
-  cf.active = 0;
-  if (in_range) {
-    prob = a.tprob ? a.tprob[tile] : 0;
-    cf = a.coef[prob];
-  }
-  bool live = in_range && cf.active;
-  if (!__syncthreads_or(live)) return;
-  const int cOwn = half ? 3 : 0, cOut = half ? 0 : 3;
-  const R sH = a.sH;
-  const R sIn = half ? sH : R(1);
-  const R sOut = half ? R(1) : sH;
-  const R pec = half ? R(0) : R(-2);
-  R G[9], sv = 0;
-  int32_t code[2] = {NBR_PEC, NBR_PEC};
-  R fn[2][3], fk1[2], fk2[2];
-#pragma unroll
-  for (int m = 0; m < 9; ++m) G[m] = 0;
-#pragma unroll
-  for (int ff = 0; ff < 2; ++ff) fn[ff][0] = fn[ff][1] = fn[ff][2] = fk1[ff] = fk2[ff] = 0;
-  if (live) {
-    const R* gv = a.gvol + tile * GV * TILE + lane;
-#pragma unroll
-    for (int m = 0; m < 9; ++m) G[m] = gv[m * TILE];
-    sv = half ? -gv[9 * TILE] : gv[10 * TILE] * sOut;
-#pragma unroll
-    for (int ff = 0; ff < 2; ++ff) {
-      const int f = 2 * g + ff;
-      code[ff] = a.nbr[(tile * 4 + f) * TILE + lane];
-      const R* gf = a.gface + (tile * 4 + f) * GF * TILE + lane;
-      fn[ff][0] = gf[0];
-      fn[ff][1] = gf[TILE];
-      fn[ff][2] = gf[2 * TILE];
-      fk1[ff] = gf[(3 + 2 * half) * TILE] * sOut;
-      fk2[ff] = gf[(4 + 2 * half) * TILE] * sOut;
-    }
-  }
-  grid_dep_wait();
-  if (live && a.pactive && !a.pactive[prob]) live = false;
-  if (!__syncthreads_or(live)) return;
-
-  const uint32_t barB = smem_addr(&bars[0]), barM = smem_addr(&bars[1]);
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barB));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barM));
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(barB), "r"(TC_B_BYTES) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-            smem_addr(sB)),
-        "l"(gTcB), "r"(TC_B_BYTES), "r"(barB)
-        : "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
-                 "r"(TC_COLS));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
-  }
-
-  const int64_t off = tile * VS + cOut * NP * TILE + lane;
-  if (live) {
-    const R* vin = a.vin + tile * VS + cOwn * NP * TILE + lane;
-#pragma unroll 4
-    for (int k = g * (3 * NP / 2); k < (g + 1) * (3 * NP / 2); ++k) cp_async_4(fs + k * RW, vin + k * TILE);
-#pragma unroll
-    for (int ff = 0; ff < 2; ++ff) {
-      const int f = 2 * g + ff;
-      if (code[ff] >= 0) {
-        const int64_t kk = int64_t(code[ff] >> 5);
-        const R* nb = a.vin + (kk >> 5) * VS + cOwn * NP * TILE + (kk & 31);
-        const int tab = (((code[ff] >> 3) & 3) * 6 + (code[ff] & 7)) * NFP;
-#pragma unroll
-        for (int jf = 0; jf < NFP; ++jf) {
-          const int nn = cNB[tab + jf];
-#pragma unroll
-          for (int c = 0; c < 3; ++c) cp_async_4(tr + ((f * NFP + jf) * 3 + c) * RW, nb + (c * NP + nn) * TILE);
-        }
-      }
-    }
-    if (a.out) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int ii = 0; ii < NH; ++ii) {
-          const int k = c * NP + g * NH + ii;
-          cp_async_4(bs + k * RW, a.base + off + k * TILE);
-        }
-    }
-    if (a.acc_out) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int ii = 0; ii < NH; ++ii) {
-          const int k = c * NP + g * NH + ii;
-          cp_async_4(acc_s + k * RW, a.acc_in + off + k * TILE);
-        }
-    }
-  }
-  cp_async_commit();
-  cp_async_wait_all();
-  tc_fence_before();
-  __syncthreads();  // own field and traces in shared memory, TMEM address, mbarriers
-  tc_fence_after();
-  const uint32_t tmem = tmem_base;
-  const uint32_t trow = tmem + (uint32_t((warp & 3) * 32) << 16);
-
-  // Volume A: chunk j of the 3 KV / 8 chunks (component j / VCH, columns 8 (j mod VCH) ..).
-  constexpr int VCH = TC_KV / 8;
-#pragma unroll 1
-  for (int j = g; j < 3 * VCH; j += 2) {
-    const int c = j / VCH, k0 = (j % VCH) * 8;
-    uint32_t hi[8], lo[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const R x = (live && k0 + k < NP) ? sIn * fs[(c * NP + k0 + k) * RW] : R(0);
-      tf32_split(x, hi[k], lo[k]);
-    }
-    tmem_st8(trow + TC_COL_AV + c * 2 * TC_KV + k0, hi);
-    tmem_st8(trow + TC_COL_AV + c * 2 * TC_KV + TC_KV + k0, lo);
-  }
-  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-  tc_fence_before();
-  __syncthreads();
-  bool okB = true;
-  if (tid == 0) {
-    tc_fence_after();
-    okB = mbar_wait(barB, 0);
-    if (okB) {
-      const uint32_t b0 = smem_addr(sB);
-      constexpr uint32_t SBO_V = (TC_KV / 4) * 128;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const uint32_t d = tmem + TC_COL_ACCV + c * TC_NV;
-#pragma unroll
-        for (int s = 0; s < TC_KV / 8; ++s) {
-          const uint32_t ahi = tmem + TC_COL_AV + c * 2 * TC_KV + 8 * s, alo = ahi + TC_KV;
-          const uint64_t bhi = tc_desc(b0 + 256 * s, 128, SBO_V);
-          const uint64_t blo = tc_desc(b0 + TC_BV_BYTES + 256 * s, 128, SBO_V);
-          tc_mma(d, alo, bhi, IDV, s > 0 ? 1u : 0u);
-          tc_mma(d, ahi, blo, IDV, 1u);
-          tc_mma(d, ahi, bhi, IDV, 1u);
-        }
-      }
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(barM)
-                 : "memory");
-  }
-
-  // Fluxes of this group's faces (overlapping the volume MMAs), over the trace slots.
-#pragma unroll 1
-  for (int ff = 0; ff < 2; ++ff) {
-    const int f = 2 * g + ff;
-    const R n0 = ff ? fn[1][0] : fn[0][0], n1 = ff ? fn[1][1] : fn[0][1], n2 = ff ? fn[1][2] : fn[0][2];
-    const R k1 = ff ? fk1[1] : fk1[0], k2 = ff ? fk2[1] : fk2[0];
-    const int32_t cd = ff ? code[1] : code[0];
-    const bool interior = cd >= 0;
-    const R bscale = cd == NBR_PEC ? pec : R(-1);
-#pragma unroll
-    for (int jf = 0; jf < NFP; ++jf) {
-      const int own = cFMt.v[f][jf];
-      R X[3], Y[3];
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const R vo = sIn * fs[(c * NP + own) * RW];
-        const R xi = interior ? sIn * tr[((f * NFP + jf) * 3 + c) * RW] - vo : bscale * vo;
-        X[c] = live ? xi : R(0);
-      }
-#pragma unroll
-      for (int c = 0; c < 3; ++c) Y[c] = __shfl_xor_sync(0xffffffffu, X[c], 1);
-      const R nY = n0 * Y[0] + n1 * Y[1] + n2 * Y[2];
-      tr[((f * NFP + jf) * 3 + 0) * RW] = k1 * (n1 * X[2] - n2 * X[1]) + k2 * (Y[0] - n0 * nY);
-      tr[((f * NFP + jf) * 3 + 1) * RW] = k1 * (n2 * X[0] - n0 * X[2]) + k2 * (Y[1] - n1 * nY);
-      tr[((f * NFP + jf) * 3 + 2) * RW] = k1 * (n0 * X[1] - n1 * X[0]) + k2 * (Y[2] - n2 * nY);
-    }
-  }
-
-  // Volume results of this group's nodes: chain rule and curl.
-  const bool okM = mbar_wait(barM, 0);
-  bool ok = __syncthreads_and(okM && okB);  // also: every group's fluxes are in shared memory
-  tc_fence_after();
-  R phi[3][NH];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int ii = 0; ii < NH; ++ii) phi[c][ii] = R(0);
-  if (ok) {
-#pragma unroll
-    for (int cp = 0; cp < 3; ++cp) {
-      float d[TC_VBLK];  // d[b NH + ii] = d F_cp / d r_b at node g NH + ii
-      tmem_ld_block<TC_VBLK>(trow + TC_COL_ACCV + cp * TC_NV + g * TC_VBLK, d);
-      const int ap = cp == 0 ? 2 : cp == 1 ? 0 : 1;
-      const int am = cp == 0 ? 1 : cp == 1 ? 2 : 0;
-      const int cpl = cp == 0 ? 1 : cp == 1 ? 2 : 0;
-      const int cmi = cp == 0 ? 2 : cp == 1 ? 0 : 1;
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const R d0 = d[ii], d1 = d[NH + ii], d2 = d[2 * NH + ii];
-        phi[cpl][ii] += G[0 * 3 + ap] * d0 + G[1 * 3 + ap] * d1 + G[2 * 3 + ap] * d2;
-        phi[cmi][ii] -= G[0 * 3 + am] * d0 + G[1 * 3 + am] * d1 + G[2 * 3 + am] * d2;
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) phi[c][ii] *= sv;
-  }
-  tc_fence_before();
-  __syncthreads();  // both groups' volume reads are complete: the lift A may overwrite those columns
-  tc_fence_after();
-
-  // Lift A: chunk j of the 3 KL / 8 chunks (component j / LCH, face-node columns 8 (j mod LCH) ..).
-  constexpr int LCH = TC_KL / 8;
-#pragma unroll 1
-  for (int j = g; j < 3 * LCH; j += 2) {
-    const int c = j / LCH, k0 = (j % LCH) * 8;
-    uint32_t hi[8], lo[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const R x = (k0 + k < 4 * NFP) ? tr[((k0 + k) * 3 + c) * RW] : R(0);
-      tf32_split(x, hi[k], lo[k]);
-    }
-    tmem_st8(trow + tc_col_al(2 * c) + k0, hi);
-    tmem_st8(trow + tc_col_al(2 * c + 1) + k0, lo);
-  }
-  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-  tc_fence_before();
-  __syncthreads();
-  if (tid == 0) {
-    tc_fence_after();
-    if (ok) {
-      const uint32_t b0 = smem_addr(sB) + 2 * TC_BV_BYTES;
-      constexpr uint32_t SBO_L = (TC_KL / 4) * 128;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const uint32_t d = tmem + TC_COL_ACCL + c * TC_NL;
-#pragma unroll
-        for (int s = 0; s < TC_KL / 8; ++s) {
-          const uint32_t ahi = tmem + tc_col_al(2 * c) + 8 * s, alo = tmem + tc_col_al(2 * c + 1) + 8 * s;
-          const uint64_t bhi = tc_desc(b0 + 256 * s, 128, SBO_L);
-          const uint64_t blo = tc_desc(b0 + TC_BL_BYTES + 256 * s, 128, SBO_L);
-          tc_mma(d, alo, bhi, IDL, s > 0 ? 1u : 0u);
-          tc_mma(d, ahi, blo, IDL, 1u);
-          tc_mma(d, ahi, bhi, IDL, 1u);
-        }
-      }
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(barM)
-                 : "memory");
-  }
-  ok = __syncthreads_and(ok && mbar_wait(barM, 1));
-  tc_fence_after();
-  if (ok) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float l[TC_LBLK];
-      tmem_ld_block<TC_LBLK>(trow + TC_COL_ACCL + c * TC_NL + g * TC_LBLK, l);
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) phi[c][ii] += l[ii];
-    }
-  }
-  tc_fence_before();
-  __syncthreads();
-  if (warp == 0) {
-    tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_COLS));
-  }
-  if (!ok) {
-    if (tid == 0 && a.err) atomicOr(a.err, 1);
-    return;
-  }
-  if (!live) return;
-
-  const int n0 = g * NH;
-  if (half && a.sigma) {  // conductivity: Phi_E -= (sigma / eps) E on this group's nodes
-    const R so = a.gvol[(tile * GV + 11) * TILE + lane];
-    const R* ev = a.vin + tile * VS + lane;
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) phi[c][ii] -= so * ev[(c * NP + n0 + ii) * TILE];
-  }
-  if (half && a.jre) add_source<R, NH>(phi, a, cf, tile, lane, n0);  // source on the E rows
-  if (a.bre) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int64_t o = off + (c * NP + n0 + ii) * TILE;
-        phi[c][ii] += cf.s_cos * a.bre[o] - cf.s_sin * a.bim[o];
-      }
-  }
-  if (a.fre) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int64_t o = off + (c * NP + n0 + ii) * TILE;
-        const R u = a.vin[o];
-        a.fre[o] += cf.fa_re * u + cf.fb_re * phi[c][ii];
-        a.fim[o] += cf.fa_im * u + cf.fb_im * phi[c][ii];
-      }
-  }
-  if (a.acc_out) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int k = c * NP + n0 + ii;
-        a.acc_out[off + k * TILE] = acc_s[k * RW] + cf.c_acc * phi[c][ii];
-      }
-  }
-  if (a.out) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int k = c * NP + n0 + ii;
-        a.out[off + k * TILE] = bs[k * RW] + cf.c_out * phi[c][ii];
-      }
-  }
-}
-
-// Dynamic shared memory of dg_stage_tc4: reference matrices, own field, trace slots, base rows,
-// and the accumulator rows of source stages (acc = true).
-constexpr size_t tc4_smem(bool acc) {
-  return size_t(TC_B_BYTES) + size_t(3 * NPQ + TRACE_SLOTS + (acc ? 6 : 3) * NPQ) * 128 * sizeof(float);
 }
 
 // Dynamic shared memory of dg_stage_tc: reference matrices, trace slots, base rows,

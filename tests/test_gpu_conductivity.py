@@ -44,7 +44,7 @@ def _rel(a, b, g):
 
 
 @pytest.mark.parametrize("q", [1, 2, 3])
-@pytest.mark.parametrize("prec,form", [("fp64", 0), ("fp64", 2), ("fp32", 2), ("fp32", 5), ("fp32", 7), ("fp32", 8)])
+@pytest.mark.parametrize("prec,form", [("fp64", 0), ("fp64", 2), ("fp32", 2), ("fp32", 5), ("fp32", 7)])
 def test_operator_and_sweeps_with_conductivity(lib, q, prec, form):
     from oracle.dg import Phi, apply_B
     from oracle.timestep import Stepper

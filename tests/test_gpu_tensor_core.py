@@ -1,5 +1,4 @@
-"""The tensor-core stage forms (stage_variant 7: two threads per tetrahedron, 8: four) against
-the FP64 oracle (GPU).
+"""The tensor-core stage form (stage_variant 7) against the FP64 oracle (GPU).
 
 The volume derivatives D_b F and the lift LIFT . f of the DG operator (Section
 5.2.2, Eq. DG_semidiscrete / Eq. ode_system) run as tcgen05 MMAs with three
@@ -24,7 +23,7 @@ from paper_2106_02858_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TC_FORMS = [7, 8]  # stage_variant of the tensor-core forms
+TC_FORMS = [7]  # stage_variant of the tensor-core form
 
 
 @pytest.fixture(scope="module")
