@@ -659,6 +659,23 @@ def profile_sweep(args):
     h.close()
 
 
+def profile_batched(args):
+    """The 32-source P3 batch on the 384-tet cube (12,288 tetrahedra per stage launch) with a
+    forced stage form: one solve capped at one CG iteration (4 sweeps: source, adjoint, and the
+    iteration's two, plus the filtered sweep); the command profiled by ncu for the tensor-core form."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2106_02858_gb300 import cmcg, inputs as I
+    prob = I.batched_rhs(nrhs=32)
+    mesh = cmcg.make_mesh(prob.mesh.verts, prob.mesh.tets, prob.mesh.tags)
+    opt = cmcg.cmcg_default_options(order=prob.order, precision=cmcg.CMCG_FP32, stage_variant=args.stage_variant)
+    h = cmcg.cmcg_create_batch([(mesh, prob.eps, prob.mu, prob.omega)] * 32, opt)
+    cmcg.cmcg_solve_batch(h, list(prob.j_re), list(prob.j_im), prob.tol, 1)
+    print(json.dumps({"profile_batched": "done", "launches": cmcg.cmcg_kernel_launches(h),
+                      "tuning": cmcg.cmcg_get_tuning(h)}))
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -672,10 +689,15 @@ def main():
     ap.add_argument("--skip-extra", action="store_true", help="skip the batched-RHS, uneven-batch and serving measurements")
     ap.add_argument("--skip-large", action="store_true", help="skip the 64^3-cube P2 request")
     ap.add_argument("--profile-sweep", action="store_true", help="run one period sweep only (for ncu)")
+    ap.add_argument("--profile-batched", action="store_true",
+                    help="one capped solve of the 32-source P3 batch only (for ncu)")
     ap.add_argument("--stage-variant", type=int, default=0, help="force a stage-kernel form (see cmcg_options)")
     args = ap.parse_args()
     if args.profile_sweep:
         profile_sweep(args)
+        return
+    if args.profile_batched:
+        profile_batched(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -291,7 +291,14 @@ int dgtd_apply(cmcg_handle* h, double t, const double* u, const double* j_re, co
 
 /* One period forward (Section 4.1.2): uT = P_{psi,w} u0 with the source j
  * (P_w if j_re is NULL).  If filt_re and filt_im are non-NULL they receive
- * the filtered field F_{psi,w} u0 (Section 5.4), double[nt][6][Np] each. */
+ * the filtered field F_{psi,w} u0 (Section 5.4), double[nt][6][Np] each.
+ * Every sweep runs the RK polynomial of Algorithms rk2 / rk4 in nested form,
+ * v <- U + (dt / k) (B v + g_k) for k = s, ..., 1; with a source, g_k is the
+ * combination of Re(J e^{i w t}) at t_m, t_m + dt/2, t_m + dt for which the
+ * nested form equals Algorithm rk4 exactly (g_4 = f(t_m), g_3 = (f(t_m) +
+ * f(t_m + dt/2)) / 2, g_2 = (f(t_m) + 2 f(t_m + dt/2)) / 3, g_1 = (f(t_m) +
+ * 4 f(t_m + dt/2) + f(t_m + dt)) / 6; for RK2 g_2 = f(t_m), g_1 = f(t_m + dt/2)),
+ * so the results differ from the printed form by rounding only. */
 int dgtd_period_forward(cmcg_handle* h, const double* u0, const double* j_re, const double* j_im, double* uT,
                         double* filt_re, double* filt_im);
 
@@ -473,8 +480,8 @@ int cmcg_fw_solve_batch(cmcg_handle* h, int periods, const double* const* j_re, 
  * every later period sweep record a CUDA event on the handle's stream before
  * its first and after its last stage; 0 stops recording.  cmcg_profile_read
  * waits for the recorded events and returns the summed sweep times and stage
- * launch counts, separately for source-free sweeps (P_w, P*_w: nested RK form)
- * and sweeps with the source or the filter (Algorithms rk2 / rk4 as printed).
+ * launch counts, separately for source-free sweeps (P_w, P*_w) and sweeps with
+ * the source or the filter (P_{psi,w}, F_{psi,w}).
  * A sweep's time covers its stage kernels back to back, launch gaps included.
  * Any output pointer may be NULL. */
 int cmcg_profile_enable(cmcg_handle* h, int on);

@@ -14,10 +14,17 @@
 //     v <- U + (dt / k) B v for k = s, ..., 1, which is the same polynomial
 //     sum_k (dt B)^k / k! as Algorithms rk2 / rk4 for a linear autonomous system
 //     and differs from them only by rounding;
-//   * sweeps with the source (P_{psi,w}, F_{psi,w}) run Algorithms rk2 / rk4 as
-//     printed, with Phi(t, U) evaluated at the stage times; the filter is
-//     accumulated on the fly at the first stage of every step and once more at
-//     t_M (Eq. filtering_RK2 / filtering_RK4, each with the 2/T of Eq. filter).
+//   * sweeps with the source (P_{psi,w}, F_{psi,w}) use the same nested form with
+//     a source term g_k added at nested stage k: for U' = B U + f(t), Algorithm
+//     rk4 gives U_{m+1} = sum_k (dt B)^k / k! U_m + dt/6 [(f1 + 4 f2 + f4)
+//     + dt B (f1 + 2 f2) + dt^2/2 B^2 (f1 + f2) + dt^3/4 B^3 f1] with f1, f2, f4
+//     the source at t_m, t_m + dt/2, t_m + dt, and v_4 = U + dt/4 (B U + g_4),
+//     v_k = U + dt/k (B v_{k+1} + g_k) reproduces it exactly with g_4 = f1,
+//     g_3 = (f1 + f2)/2, g_2 = (f1 + 2 f2)/3, g_1 = (f1 + 4 f2 + f4)/6 (Algorithm
+//     rk2 is already nested: g_2 = f1, g_1 = f2).  No accumulator vector is
+//     kept.  The first nested stage evaluates Phi(t_m, U_m) itself, so the
+//     filter is accumulated on the fly there and once more at t_M
+//     (Eq. filtering_RK2 / filtering_RK4, each with the 2/T of Eq. filter).
 // CMCG (Section 2.2, Algorithms init / grad / cmcg) runs in residual form from
 // U0 = 0 for every problem: G = P_psi 0, G* = G - P* G, R = D = G*, then per
 // iteration W_T = P D - D, A = P* W_T - W_T, alpha = |R|^2 / (D, A),
@@ -94,7 +101,7 @@ struct cmcg_handle {
   int32_t* tprob = nullptr;   // problem of each tile (nullptr when nprob == 1)
   double* inv_eps = nullptr;  // external order, problems concatenated
   // vectors
-  void *Uw = nullptr, *vA = nullptr, *vB = nullptr, *ACC = nullptr, *Fre = nullptr, *Fim = nullptr;
+  void *Uw = nullptr, *vA = nullptr, *vB = nullptr, *Fre = nullptr, *Fim = nullptr;
   void *Jre = nullptr, *Jim = nullptr;
   void *Bre = nullptr, *Bim = nullptr;  // lifted impedance-face data, all 6 rows (allocated on first use)
   void *U0 = nullptr, *Rv = nullptr, *D = nullptr, *A = nullptr, *WT = nullptr;
@@ -237,21 +244,35 @@ void filter_weights(Prob& P, int integrator) {
   }
 }
 
-// Coefficient tables.  Launch l of a sweep is stage r = l % s of step m = l / s.
-// Classic stage r of RK4 (Algorithm rk4): out = U + c_out K_{r+1} (r < 3) or
-// ACC + dt/6 K4, acc = U + dt/6 K1 (r = 0), acc += dt/3 K_{r+1} (r = 1, 2); the
-// source is evaluated at t_m + {0, dt/2, dt/2, dt}.  RK2 (Algorithm rk2): out = U
-// + dt/2 K1 (r = 0), out = U + dt K2 at t_m + dt/2 (r = 1).
+// Coefficient tables.  Launch l of a sweep is nested stage r = l % s of step m = l / s:
+// out = U + dt / (s - r) Phi.  In source sweeps Phi carries the source combination g of
+// nested stage s - r (see the top of this file): Re(J e^{i w t}) summed with the weights
+// below over the times t_m + {0, dt/2, dt} (the stage times of Algorithms rk2 / rk4).
+constexpr double SRC_OFF[3] = {0.0, 0.5, 1.0};
+constexpr double SRC_W4[4][3] = {{1.0, 0.0, 0.0}, {0.5, 0.5, 0.0}, {1.0 / 3.0, 2.0 / 3.0, 0.0},
+                                 {1.0 / 6.0, 4.0 / 6.0, 1.0 / 6.0}};
+constexpr double SRC_W2[2][3] = {{1.0, 0.0, 0.0}, {0.0, 1.0, 0.0}};
+
+// The source phase of launch r: sum_j W[r][j] (cos, sin)(w (t_m + SRC_OFF[j] dt)).
+void source_phase(int s, int r, double dt, double t_m, double w, double* cs, double* sn) {
+  const double* W = s == 4 ? SRC_W4[r] : SRC_W2[r];
+  *cs = 0.0;
+  *sn = 0.0;
+  for (int j = 0; j < 3; ++j) {
+    if (W[j] == 0.0) continue;
+    const double t = t_m + SRC_OFF[j] * dt;
+    *cs += W[j] * std::cos(w * t);
+    *sn += W[j] * std::sin(w * t);
+  }
+}
+
 template <typename R>
-void classic_coef(int s, int r, double dt, double t_m, double w, StageCoef<R>& c) {
-  static const double c4[4] = {0.5, 0.5, 1.0, 1.0 / 6.0}, a4[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 0.0},
-                      o4[4] = {0.0, 0.5, 0.5, 1.0}, c2[2] = {0.5, 1.0}, o2[2] = {0.0, 0.5};
-  const double co = s == 4 ? c4[r] : c2[r], ca = s == 4 ? a4[r] : 0.0, off = s == 4 ? o4[r] : o2[r];
-  const double t = t_m + off * dt;
-  c.c_out = R(co * dt);
-  c.c_acc = R(ca * dt);
-  c.s_cos = R(std::cos(w * t));
-  c.s_sin = R(std::sin(w * t));
+void source_coef(int s, int r, double dt, double t_m, double w, StageCoef<R>& c) {
+  double cs, sn;
+  source_phase(s, r, dt, t_m, w, &cs, &sn);
+  c.c_out = R(dt / (s - r));
+  c.s_cos = R(cs);
+  c.s_sin = R(sn);
 }
 
 template <typename R>
@@ -277,14 +298,14 @@ int build_tables(cmcg_handle* h) {
         StageCoef<R> cs = zero;
         if (m < P.M) {
           cs.active = 1;
-          classic_coef<R>(s, r, P.dt, m * P.dt, P.omega, cs);
+          source_coef<R>(s, r, P.dt, m * P.dt, P.omega, cs);
         }
         ts[size_t(l) * np_ + p] = cs;
       }
       StageCoef<R> cf = zero;
       if (m < P.M || (m == P.M && r == 0)) {  // the extra launch at t_M evaluates Phi_M for the filter
         cf.active = 1;
-        classic_coef<R>(s, r, P.dt, m * P.dt, P.omega, cf);
+        source_coef<R>(s, r, P.dt, m * P.dt, P.omega, cf);
         if (r == 0) {
           cf.fa_re = R(P.fa[m].real());
           cf.fa_im = R(P.fa[m].imag());
@@ -438,8 +459,9 @@ void sweep_free(cmcg_handle* h, bool adjoint, const int32_t* pactive) {
   prof_end(h, pe);
 }
 
-// Sweep with source (Algorithms rk2 / rk4 as printed) of Uw in place; optional
-// on-the-fly filter (one extra launch evaluates Phi at t_M).
+// Sweep with source (Algorithms rk2 / rk4 in the nested form with the source combinations
+// of source_coef) of Uw in place; optional on-the-fly filter at the first nested stage of
+// every step (one extra launch evaluates Phi at t_M).
 template <typename R>
 void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* mask = nullptr) {
   Range rg(filter ? "cmcg: filtered source sweep" : "cmcg: source sweep");
@@ -447,7 +469,6 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
   R* Uw = (R*)h->Uw;
   R* vA = (R*)h->vA;
   R* vB = (R*)h->vB;
-  R* ACC = (R*)h->ACC;
   const int s = h->s;
   const int L = filter ? h->L_srcf : h->L_src;
   const int K = with_source ? h->mf_nharm : 0;
@@ -457,20 +478,9 @@ void sweep_source(cmcg_handle* h, bool with_source, bool filter, const int32_t* 
   for (int l = 0; l < L; ++l) {
     const int r = l % s;
     StageArgs<R> a = blank<R>();
-    if (s == 2) {
-      a.vin = r == 0 ? Uw : vA;
-      a.base = Uw;
-      a.out = r == 0 ? vA : Uw;
-    } else {
-      R* vin_of[4] = {Uw, vA, vB, vA};
-      a.vin = vin_of[r];
-      a.base = r == 3 ? ACC : Uw;
-      a.out = r == 0 ? vA : r == 1 ? vB : r == 2 ? vA : Uw;
-      if (r < 3) {
-        a.acc_in = r == 0 ? Uw : ACC;
-        a.acc_out = ACC;
-      }
-    }
+    a.vin = r == 0 ? Uw : (r % 2 == 1 ? vA : vB);  // the buffers of sweep_free
+    a.base = Uw;
+    a.out = r == s - 1 ? Uw : (r % 2 == 0 ? vA : vB);
     if (with_source) {
       a.jre = (const R*)(K > 0 ? h->Jm_re : h->Jre);
       a.jim = (const R*)(K > 0 ? h->Jm_im : h->Jim);
@@ -877,16 +887,16 @@ int solve_multi_dev(cmcg_handle* h, int K, const int* harm, const double* const*
     if (cudaMalloc(&h->mf_tab, size_t(h->L_srcf) * sizeof(StageCoef<R>)) != cudaSuccess) return CMCG_ERR_OUT_OF_MEMORY;
     h->bytes += size_t(h->L_srcf) * sizeof(StageCoef<R>);
   }
-  // cos / sin of every harmonic at every launch's stage time (the stage offsets of Algorithms rk2 / rk4)
+  // source phase of every harmonic at every launch (the nested-stage combination of source_coef)
   const int s = h->s;
-  static const double off4[4] = {0.0, 0.5, 0.5, 1.0}, off2[2] = {0.0, 0.5};
   std::vector<R> hcs(static_cast<size_t>(h->L_srcf) * 2 * K);
   for (int l = 0; l < h->L_srcf; ++l) {
     const int m = l / s, r = l % s;
-    const double t = (m + (s == 4 ? off4[r] : off2[r])) * P.dt;
     for (int k = 0; k < K; ++k) {
-      hcs[(size_t(l) * K + k) * 2] = R(std::cos(harm[k] * P.omega * t));
-      hcs[(size_t(l) * K + k) * 2 + 1] = R(std::sin(harm[k] * P.omega * t));
+      double cs, sn;
+      source_phase(s, r, P.dt, m * P.dt, harm[k] * P.omega, &cs, &sn);
+      hcs[(size_t(l) * K + k) * 2] = R(cs);
+      hcs[(size_t(l) * K + k) * 2 + 1] = R(sn);
     }
   }
   CK(cudaMemcpyAsync(h->mf_hcs, hcs.data(), hcs.size() * sizeof(R), cudaMemcpyHostToDevice, h->stream));
@@ -917,7 +927,7 @@ int solve_multi_dev(cmcg_handle* h, int K, const int* harm, const double* const*
       std::memset(&c, 0, sizeof(c));
       if (m < Pk.M || (m == Pk.M && r == 0)) {
         c.active = 1;
-        classic_coef<R>(s, r, Pk.dt, m * Pk.dt, Pk.omega, c);
+        source_coef<R>(s, r, Pk.dt, m * Pk.dt, Pk.omega, c);
         if (r == 0) {
           c.fa_re = R(Pk.fa[m].real());
           c.fa_im = R(Pk.fa[m].imag());
@@ -1134,7 +1144,7 @@ void free_all(cmcg_handle* h) {
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->cap_stream = nullptr;
   void* ptrs[] = {h->Jm_re, h->Jm_im, h->mf_hcs, h->mf_tab, h->mf_src,
-                  h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB, h->ACC,
+                  h->gvol, h->gface, h->nbr, h->wdot, h->e_of_i, h->tprob, h->inv_eps, h->Uw, h->vA, h->vB,
                   h->Fre, h->Fim, h->Jre, h->Jim, h->Bre, h->Bim, h->U0, h->Rv, h->D, h->A, h->WT, h->partials, h->sc, h->pactive,
                   h->bt_tet0, h->bt_ntet, h->bt_prob, h->bt_pb0, h->tab_free, h->tab_src, h->tab_srcf, h->tab_one,
                   h->ext0, h->ext1, h->ext2, h->ext3, h->used, h->err, h->slot_masks, h->halo_dst, h->halo_src, h->g_in,
@@ -1310,7 +1320,7 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
 
   auto alloc = [&](void** p, size_t n) -> bool { return cudaMalloc(p, n) == cudaSuccess; };
   const size_t vb = h->nvec * h->rsize, jb = h->njvec * h->rsize;
-  bool ok = alloc(&h->Uw, vb) && alloc(&h->vA, vb) && alloc(&h->vB, vb) && alloc(&h->ACC, vb) && alloc(&h->Fre, vb) &&
+  bool ok = alloc(&h->Uw, vb) && alloc(&h->vA, vb) && alloc(&h->vB, vb) && alloc(&h->Fre, vb) &&
             alloc(&h->Fim, vb) && alloc(&h->Jre, jb) && alloc(&h->Jim, jb) && alloc(&h->U0, vb) &&
             alloc(&h->Rv, vb) && alloc(&h->D, vb) && alloc(&h->A, vb) && alloc(&h->WT, vb) &&
             alloc((void**)&h->partials, sizeof(double) * 2 * std::max<size_t>(1, bt_tet0.size())) &&
@@ -1324,7 +1334,7 @@ int create_impl(int nprob, const cmcg_problem* probs, const cmcg_options* opt_in
       cudaMallocHost((void**)&h->used_host, sizeof(int32_t) * nprob) != cudaSuccess ||
       cudaMallocHost((void**)&h->err_host, sizeof(int32_t)) != cudaSuccess)
     return fail(CMCG_ERR_OUT_OF_MEMORY);
-  if (cudaMemset(h->ACC, 0, vb) != cudaSuccess || cudaMemset(h->err, 0, sizeof(int32_t)) != cudaSuccess)
+  if (cudaMemset(h->err, 0, sizeof(int32_t)) != cudaSuccess)
     return fail(CMCG_ERR_CUDA);
   rc = h->prec == CMCG_FP32 ? build_tables<float>(h) : build_tables<double>(h);
   if (rc) return fail(rc);

@@ -112,13 +112,14 @@ constexpr int32_t NBR_IMP = -2;
 //   Phi   = src + B_sigma(vin),  src = s_cos * (jre + bre) - s_sin * (jim + bim)   (B_sigma = Sigma B Sigma when sH = -1;
 //           B carries -(sigma/eps) E on the E rows when a.sigma is set)
 //   out   = base + c_out Phi        (skipped if out == nullptr)
-//   acc_o = acc_i + c_acc Phi       (skipped if acc_o == nullptr)
 //   F    += fa vin + fb Phi         (complex weights; skipped if fre == nullptr)
+// (s_cos, s_sin) are the cos / sin of the source phase at the stage time, or the
+// weighted sums of them that the nested RK form of a source sweep adds per stage.
 // A problem whose entry has active == 0 leaves everything untouched.
 template <typename R>
 struct StageCoef {
-  R c_out, c_acc, s_cos, s_sin, fa_re, fa_im, fb_re, fb_im;
-  int32_t active, pad;
+  R c_out, s_cos, s_sin, fa_re, fa_im, fb_re, fb_im;
+  int32_t active;
 };
 
 // Arguments of one RK stage over all tetrahedra of all problems of a handle.
@@ -127,8 +128,6 @@ struct StageArgs {
   const R* vin;
   const R* base;
   R* out;
-  const R* acc_in;
-  R* acc_out;
   const R* jre;  // E-rows source / eps, [tile][3][Np][32] (null: no source)
   const R* jim;
   const R* bre;  // lifted impedance-face data, all 6 rows in the field layout (null: none)

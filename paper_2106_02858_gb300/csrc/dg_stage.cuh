@@ -124,6 +124,33 @@ __device__ __forceinline__ void add_source(R (&phi)[3][NN], const StageArgs<R>& 
   }
 }
 
+// The on-the-fly filter on this thread's output rows n0 .. n0 + NN - 1 (forward sweeps with the
+// filter, first nested stage of each step): F += fa U + fb Phi.  Each component's rows of U and F
+// are loaded before any of them is stored: vin, fre and fim are not known to be distinct, and a
+// row-by-row read-modify-write would put every load behind the previous row's stores.
+template <typename R, int NN>
+__device__ __forceinline__ void accumulate_filter(const StageArgs<R>& a, const StageCoef<R>& cf,
+                                                  const R (&phi)[3][NN], int64_t off, int n0) {
+  constexpr int NP = NPQ;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    R u[NN], fr[NN], fi[NN];
+#pragma unroll
+    for (int ii = 0; ii < NN; ++ii) {
+      const int64_t o = off + (c * NP + n0 + ii) * TILE;
+      u[ii] = a.vin[o];
+      fr[ii] = a.fre[o];
+      fi[ii] = a.fim[o];
+    }
+#pragma unroll
+    for (int ii = 0; ii < NN; ++ii) {
+      const int64_t o = off + (c * NP + n0 + ii) * TILE;
+      a.fre[o] = fr[ii] + (cf.fa_re * u[ii] + cf.fb_re * phi[c][ii]);
+      a.fim[o] = fi[ii] + (cf.fa_im * u[ii] + cf.fb_im * phi[c][ii]);
+    }
+  }
+}
+
 // MINB: minimum resident blocks per SM requested from the compiler (caps registers at
 // 65536 / (MINB * STAGE_THREADS)); the forms are timed per handle (see api.cu).
 template <typename R, int MINB>
@@ -207,14 +234,17 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
       }
     }
   }
-  // Source stages (classic RK form): the accumulator rows this thread updates at the end,
-  // fetched now so that their latency overlaps the volume and face work.
-  R* acc_s = tr + TRACE_SLOTS * STAGE_THREADS;
-  if (a.acc_out) {
+  // Single-frequency source stages: the tetrahedron's source rows, J_re by the lane that adds
+  // the source (half = 1) and J_im by its partner, fetched now so that their latency overlaps
+  // the volume and face work.
+  R* js = tr + TRACE_SLOTS * STAGE_THREADS;
+  const bool jpre = a.jre && a.nharm <= 0;
+  if (jpre) {
+    const R* src = (half ? a.jre : a.jim) + tile * (3 * NP * TILE) + lane;
 #pragma unroll
     for (int k = 0; k < 3 * NP; ++k) {
-      if constexpr (sizeof(R) == 4) cp_async_4(acc_s + k * STAGE_THREADS, a.acc_in + off + k * TILE);
-      else cp_async_8(acc_s + k * STAGE_THREADS, a.acc_in + off + k * TILE);
+      if constexpr (sizeof(R) == 4) cp_async_4(js + k * STAGE_THREADS, src + k * TILE);
+      else cp_async_8(js + k * STAGE_THREADS, src + k * TILE);
     }
   }
   cp_async_commit();
@@ -247,6 +277,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
   }
 
   cp_async_wait_all();
+  __syncwarp();  // the partner's prefetched source rows are read at the end
   // The face term in two passes: first every face node's flux (24 independent
   // chains of trace read, jump, partner shuffle and flux, stored over the trace
   // slots the thread owns), then the lift as a stream of FMAs.  The values and
@@ -301,7 +332,17 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
 #pragma unroll
       for (int n = 0; n < NP; ++n) phi[c][n] -= so * ev[(c * NP + n) * TILE];
   }
-  if (half && a.jre) add_source<R, NP>(phi, a, cf, tile, lane, 0);  // source on the E rows
+  if (half && jpre) {  // source on the E rows: J_re in this thread's slots, J_im in the partner's
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        const int k = (c * NP + n) * STAGE_THREADS;
+        phi[c][n] += cf.s_cos * js[k] - cf.s_sin * js[k - 1];
+      }
+  } else if (half && a.jre) {
+    add_source<R, NP>(phi, a, cf, tile, lane, 0);
+  }
   if (a.bre) {  // impedance-face data, lifted onto this thread's output rows (source sweeps only)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -311,26 +352,7 @@ __global__ void __launch_bounds__(STAGE_THREADS, MINB) dg_stage_kernel(const Sta
         phi[c][n] += cf.s_cos * a.bre[o] - cf.s_sin * a.bim[o];
       }
   }
-  if (a.fre) {  // forward sweeps only: F += fa U + fb Phi on this thread's output rows
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        const int64_t o = off + (c * NP + n) * TILE;
-        const R u = a.vin[o];
-        a.fre[o] += cf.fa_re * u + cf.fb_re * phi[c][n];
-        a.fim[o] += cf.fa_im * u + cf.fb_im * phi[c][n];
-      }
-  }
-  if (a.acc_out) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        const int64_t o = off + (c * NP + n) * TILE;
-        a.acc_out[o] = acc_s[(c * NP + n) * STAGE_THREADS] + cf.c_acc * phi[c][n];
-      }
-  }
+  if (a.fre) accumulate_filter<R, NP>(a, cf, phi, off, 0);  // forward sweeps with the filter only
   if (a.out) {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -566,26 +588,7 @@ __device__ __forceinline__ void quad_stage(const StageArgs<R>& a) {
         phi[c][ii] += cf.s_cos * a.bre[o] - cf.s_sin * a.bim[o];
       }
   }
-  if (a.fre) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int64_t o = off + (c * NP + I0 + ii) * TILE;
-        const R u = a.vin[o];
-        a.fre[o] += cf.fa_re * u + cf.fb_re * phi[c][ii];
-        a.fim[o] += cf.fa_im * u + cf.fb_im * phi[c][ii];
-      }
-  }
-  if (a.acc_out) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int ii = 0; ii < NH; ++ii) {
-        const int64_t o = off + (c * NP + I0 + ii) * TILE;
-        a.acc_out[o] = a.acc_in[o] + cf.c_acc * phi[c][ii];
-      }
-  }
+  if (a.fre) accumulate_filter<R, NH>(a, cf, phi, off, I0);
   if (a.out) {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -608,11 +611,15 @@ __global__ void __launch_bounds__(QD_THREADS, MINB) dg_stage_quad(const StageArg
 
 }  // namespace
 
-// Dynamic shared memory of the two-thread kernel: the trace slots, plus the accumulator
-// rows in source stages (acc = true).
+// Dynamic shared memory of the two-thread kernel: the trace slots, plus the prefetched
+// source rows in single-frequency source stages (src = true).
 template <typename R>
-constexpr size_t stage_smem(bool acc = false) {
-  return size_t(TRACE_SLOTS + (acc ? 3 * NPQ : 0)) * STAGE_THREADS * sizeof(R);
+constexpr size_t stage_smem(bool src = false) {
+  return size_t(TRACE_SLOTS + (src ? 3 * NPQ : 0)) * STAGE_THREADS * sizeof(R);
+}
+template <typename R>
+bool prefetches_source(const StageArgs<R>& a) {
+  return a.jre != nullptr && a.nharm <= 0;
 }
 
 template <typename Arg>
@@ -635,7 +642,7 @@ template <>
 void launch_stage<CMCG_Q, float>(const StageArgs<float>& a, cudaStream_t s, int form, bool pdl) {
   const unsigned blocks = unsigned((2 * a.nti + STAGE_THREADS - 1) / STAGE_THREADS);
   const unsigned qblocks = unsigned(a.nti / TILE);  // one block per tile
-  const size_t sm = stage_smem<float>(a.acc_out != nullptr);
+  const size_t sm = stage_smem<float>(prefetches_source(a));
   constexpr size_t qsm = quad_smem<float>();
   switch (form) {
     case 1: launch_k(dg_stage_kernel<float, 3>, blocks, STAGE_THREADS, sm, s, pdl, a); break;
@@ -645,7 +652,7 @@ void launch_stage<CMCG_Q, float>(const StageArgs<float>& a, cudaStream_t s, int 
     case 5: launch_k(dg_stage_quad<float, 6>, qblocks, QD_THREADS, qsm, s, pdl, a); break;
     case STAGE_FORM_TC:
       launch_k(dg_stage_tc<TC_MINB>, unsigned((a.nti + TC_TETS - 1) / TC_TETS), TC_THREADS,
-               tc_smem(a.acc_out != nullptr), s, pdl, a);
+               tc_smem(prefetches_source(a)), s, pdl, a);
       break;
     default: launch_k(dg_stage_kernel<float, 1>, blocks, STAGE_THREADS, sm, s, pdl, a); break;
   }
@@ -658,7 +665,7 @@ void launch_stage<CMCG_Q, double>(const StageArgs<double>& a, cudaStream_t s, in
   switch (form) {
     case 1: launch_k(dg_stage_quad<double, 2>, qblocks, QD_THREADS, qsm, s, pdl, a); break;
     case 2: launch_k(dg_stage_quad<double, 3>, qblocks, QD_THREADS, qsm, s, pdl, a); break;
-    default: launch_k(dg_stage_kernel<double, 1>, blocks, STAGE_THREADS, stage_smem<double>(a.acc_out != nullptr), s, pdl, a); break;
+    default: launch_k(dg_stage_kernel<double, 1>, blocks, STAGE_THREADS, stage_smem<double>(prefetches_source(a)), s, pdl, a); break;
   }
 }
 
@@ -675,6 +682,8 @@ void upload_constants<CMCG_Q>(const RefMats& rm) {
   cudaFuncSetAttribute(dg_stage_quad<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<double>()));
   cudaFuncSetAttribute(dg_stage_quad<double, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(quad_smem<double>()));
   cudaFuncSetAttribute(dg_stage_tc<TC_MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(tc_smem(true)));
+  cudaFuncSetAttribute(dg_stage_tc<TC_MINB>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                       int(cudaSharedmemCarveoutMaxShared));  // two P3 CTAs per SM need 2 x 113 KB
   tc_upload_reference(rm);
   const int np = rm.np, nfp = rm.nfp;
   std::vector<double> D(3 * np * np);

@@ -27,8 +27,10 @@
 // (the lo_a lo_b term, ~2^-22 relative, is dropped), accumulated in FP32 in TMEM.
 // The reference matrices are split on the host from double (both parts rounded).
 //
-// Synchronisation.  One thread issues every MMA of the CTA and commits them to
-// an mbarrier; all waits on mbarriers are bounded (about one second of
+// Synchronisation.  One thread issues every MMA of the CTA; the six contractions
+// (volume of own components 0, 1, 2, then lift of output components 0, 1, 2) use
+// two TMEM buffers in turn, each with its own mbarrier, so that at most 256 TMEM
+// columns are held and two CTAs can share an SM.  All waits on mbarriers are bounded (about one second of
 // %globaltimer), after which the CTA records CMCG_ERR_DEVICE_TIMEOUT in a.err,
 // skips the dependent work, frees its TMEM and returns.  TMEM is allocated after
 // the grid-dependency wait, so a CTA that starts early under programmatic
@@ -53,21 +55,15 @@ __host__ __device__ constexpr int tc_vcol(int b, int i) {
   return (i / TC_NH) * TC_VBLK + b * TC_NH + (i % TC_NH);
 }
 __host__ __device__ constexpr int tc_lcol(int i) { return (i / TC_NH) * TC_LBLK + (i % TC_NH); }
-// TMEM columns: [volume accumulators 3 NV | lift accumulators 3 NL | volume A 6 KV];
-// the six lift A blocks (hi, lo per component, KL columns each) reuse the volume
-// accumulator and volume A columns once the volume results have been read.
-constexpr int TC_COL_ACCV = 0;
-constexpr int TC_COL_ACCL = 3 * TC_NV;
-constexpr int TC_COL_AV = 3 * TC_NV + 3 * TC_NL;
-constexpr int TC_COLS_USED = TC_COL_AV + 6 * TC_KV;
-constexpr int TC_COLS = TC_COLS_USED <= 32 ? 32 : TC_COLS_USED <= 64 ? 64 : TC_COLS_USED <= 128 ? 128
-                        : TC_COLS_USED <= 256 ? 256 : 512;
-constexpr int TC_AL_FIRST = (3 * TC_NV) / TC_KL;  // lift A blocks that fit in the volume accumulator columns
-static_assert(TC_COLS_USED <= 512, "TMEM columns");
-static_assert(6 - TC_AL_FIRST <= (6 * TC_KV) / TC_KL, "lift A blocks must fit in the freed columns");
-__host__ __device__ constexpr int tc_col_al(int blk) {
-  return blk < TC_AL_FIRST ? blk * TC_KL : TC_COL_AV + (blk - TC_AL_FIRST) * TC_KL;
-}
+// TMEM columns: two buffers of TC_BUF columns.  A buffer holds one component's
+// contraction: its accumulator [0, N) and its A operand, hi [N, N + K) and lo
+// [N + K, N + 2K) -- volume (N = NV, K = KV) or lift (N = NL, K = KL).  The six
+// contractions (3 volume, then 3 lift) alternate between the buffers, so one
+// component's MMAs run while the previous component's result is read.
+constexpr int TC_NEED = (TC_NV + 2 * TC_KV) > (TC_NL + 2 * TC_KL) ? (TC_NV + 2 * TC_KV) : (TC_NL + 2 * TC_KL);
+constexpr int TC_BUF = TC_NEED <= 32 ? 32 : TC_NEED <= 64 ? 64 : TC_NEED <= 128 ? 128 : 256;
+constexpr int TC_COLS = 2 * TC_BUF;
+static_assert(TC_COLS <= 256, "two CTAs per SM need at most 256 TMEM columns each");
 
 // Reference matrices for the MMAs (B operands), split hi / lo, in the core-matrix
 // layout: [BV hi | BV lo | BL hi | BL lo], BV = NV x KV, BL = NL x KL (row-major
@@ -172,13 +168,14 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
   const int lane = int(gt & 31);
   const bool in_range = gt < a.nti;  // warp-uniform (nti is a multiple of 32)
 
-  __shared__ __align__(8) uint64_t bars[2];  // [0]: reference matrices loaded, [1]: MMA phases
+  __shared__ __align__(8) uint64_t bars[3];  // [0]: reference matrices loaded, [1 + b]: MMAs of buffer b
   __shared__ uint32_t tmem_base;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* sB = smem_raw;                                            // TC_B_BYTES
   R* tr = reinterpret_cast<R*>(smem_raw + TC_B_BYTES) + tid;               // trace / flux slots
   R* bs = tr + TRACE_SLOTS * TC_THREADS;                                   // base rows
-  R* acc_s = bs + 3 * NP * TC_THREADS;                                     // accumulator rows (source stages)
+  R* js = bs + 3 * NP * TC_THREADS;  // source rows (single-frequency source stages): J_re (half 1), J_im (half 0)
+  const bool jpre = a.jre && a.nharm <= 0;
 
   int prob = 0;
   StageCoef<R> cf;
@@ -221,10 +218,12 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
   if (live && a.pactive && !a.pactive[prob]) live = false;  // CG converged (written by the CG kernels)
   if (!__syncthreads_or(live)) return;
 
-  const uint32_t barB = smem_addr(&bars[0]), barM = smem_addr(&bars[1]);
+  const uint32_t barB = smem_addr(&bars[0]);
+  const uint32_t barM[2] = {smem_addr(&bars[1]), smem_addr(&bars[2])};
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barB));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barM));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barM[0]));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barM[1]));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     // the reference matrices: one bulk copy, completion counted in bytes on barB
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(barB), "r"(TC_B_BYTES) : "memory");
@@ -272,9 +271,10 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
 #pragma unroll
       for (int k = 0; k < 3 * NP; ++k) cp_async_4(bs + k * TC_THREADS, a.base + off + k * TILE);
     }
-    if (a.acc_out) {
+    if (jpre) {
+      const R* src = (half ? a.jre : a.jim) + tile * (3 * NP * TILE) + lane;
 #pragma unroll
-      for (int k = 0; k < 3 * NP; ++k) cp_async_4(acc_s + k * TC_THREADS, a.acc_in + off + k * TILE);
+      for (int k = 0; k < 3 * NP; ++k) cp_async_4(js + k * TC_THREADS, src + k * TILE);
     }
   }
   cp_async_commit();
@@ -285,9 +285,9 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
   const uint32_t tmem = tmem_base;
   const uint32_t trow = tmem + (uint32_t(warp * 32) << 16);  // this warp's TMEM lanes
 
-  // Volume A: own field components, split hi / lo, zero-padded to KV columns.
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
+  const uint32_t sb = smem_addr(sB);
+  // Volume A of component c into buffer b: the own field, split hi / lo, zero-padded to KV columns.
+  auto store_vol_a = [&](int b, int c) {
 #pragma unroll
     for (int k0 = 0; k0 < TC_KV; k0 += 8) {
       uint32_t hi[8], lo[8];
@@ -300,10 +300,105 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
           lo[k] = 0u;
         }
       }
-      tmem_st8(trow + TC_COL_AV + c * 2 * TC_KV + k0, hi);
-      tmem_st8(trow + TC_COL_AV + c * 2 * TC_KV + TC_KV + k0, lo);
+      tmem_st8(trow + b * TC_BUF + TC_NV + k0, hi);
+      tmem_st8(trow + b * TC_BUF + TC_NV + TC_KV + k0, lo);
     }
-  }
+  };
+  // Lift A of output component c into buffer b: the face fluxes (in the trace slots), split.
+  auto store_lift_a = [&](int b, int c) {
+#pragma unroll
+    for (int k0 = 0; k0 < TC_KL; k0 += 8) {
+      uint32_t hi[8], lo[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (k0 + k < 4 * NFP) {
+          tf32_split(tr[((k0 + k) * 3 + c) * TC_THREADS], hi[k], lo[k]);
+        } else {
+          hi[k] = 0u;
+          lo[k] = 0u;
+        }
+      }
+      tmem_st8(trow + b * TC_BUF + TC_NL + k0, hi);
+      tmem_st8(trow + b * TC_BUF + TC_NL + TC_KL + k0, lo);
+    }
+  };
+  // MMAs of buffer b (thread 0): D = A_lo B_hi + A_hi B_lo + A_hi B_hi over the K steps,
+  // then a commit to the buffer's mbarrier (also when skipped, so that waiters are released).
+  auto issue = [&](int b, bool lift, bool go) {
+    if (go) {
+      const uint32_t d = tmem + b * TC_BUF;
+      const uint32_t nacc = lift ? TC_NL : TC_NV;
+      const int K = lift ? TC_KL : TC_KV;
+      const uint32_t b0 = sb + (lift ? 2 * TC_BV_BYTES : 0);
+      const uint32_t blo_off = lift ? TC_BL_BYTES : TC_BV_BYTES;
+      const uint32_t sbo = uint32_t(K / 4) * 128;
+      const uint32_t idesc = lift ? IDL : IDV;
+#pragma unroll 1
+      for (int s8 = 0; s8 < K / 8; ++s8) {
+        const uint32_t ahi = d + nacc + 8 * s8, alo = ahi + K;
+        const uint64_t bhi = tc_desc(b0 + 256 * s8, 128, sbo);
+        const uint64_t blo = tc_desc(b0 + blo_off + 256 * s8, 128, sbo);
+        tc_mma(d, alo, bhi, idesc, s8 > 0 ? 1u : 0u);
+        tc_mma(d, ahi, blo, idesc, 1u);
+        tc_mma(d, ahi, bhi, idesc, 1u);
+      }
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(barM[b])
+                 : "memory");
+  };
+  // All A operands written and all accumulator reads done before thread 0 issues MMAs.
+  auto handoff = [&](bool ok_in) -> bool {
+    asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+    tc_fence_before();
+    const bool r = __syncthreads_and(ok_in);
+    tc_fence_after();
+    return r;
+  };
+  R phi[3][NP];
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+#pragma unroll
+    for (int i = 0; i < NP; ++i) phi[c][i] = R(0);
+  // Volume result of own component cp (buffer b): derivatives along r, s, t, chain rule, curl.
+  auto read_vol = [&](int b, int cp) {
+    float d[TC_NV];
+#pragma unroll
+    for (int k0 = 0; k0 < TC_NV; k0 += 16) {
+      float t16[16];
+      tmem_ld16(trow + b * TC_BUF + k0, t16);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) d[k0 + k] = t16[k];
+    }
+    // curl F: component 0 = d1 F2 - d2 F1, 1 = d2 F0 - d0 F2, 2 = d0 F1 - d1 F0
+    const int ap = cp == 0 ? 2 : cp == 1 ? 0 : 1;   // axis whose derivative enters with +
+    const int am = cp == 0 ? 1 : cp == 1 ? 2 : 0;   // axis whose derivative enters with -
+    const int cpl = cp == 0 ? 1 : cp == 1 ? 2 : 0;  // output component receiving + d_ap F_cp
+    const int cmi = cp == 0 ? 2 : cp == 1 ? 0 : 1;  // output component receiving - d_am F_cp
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      const R d0 = d[tc_vcol(0, i)], d1 = d[tc_vcol(1, i)], d2 = d[tc_vcol(2, i)];
+      const R dp = G[0 * 3 + ap] * d0 + G[1 * 3 + ap] * d1 + G[2 * 3 + ap] * d2;
+      const R dm = G[0 * 3 + am] * d0 + G[1 * 3 + am] * d1 + G[2 * 3 + am] * d2;
+      phi[cpl][i] += dp;
+      phi[cmi][i] -= dm;
+    }
+  };
+  auto read_lift = [&](int b, int c) {
+    float l[TC_NL];
+#pragma unroll
+    for (int k0 = 0; k0 < TC_NL; k0 += 16) {
+      float t16[16];
+      tmem_ld16(trow + b * TC_BUF + k0, t16);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) l[k0 + k] = t16[k];
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) phi[c][i] += l[tc_lcol(i)];
+  };
+
+  // Volume contractions of components 0 and 1 (buffers 0, 1).
+  store_vol_a(0, 0);
+  store_vol_a(1, 1);
   asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
   tc_fence_before();
   __syncthreads();
@@ -311,25 +406,8 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
   if (tid == 0) {
     tc_fence_after();
     okB = mbar_wait(barB, 0);
-    if (okB) {
-      const uint32_t b0 = smem_addr(sB);
-      constexpr uint32_t SBO_V = (TC_KV / 4) * 128;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const uint32_t d = tmem + TC_COL_ACCV + c * TC_NV;
-#pragma unroll
-        for (int s = 0; s < TC_KV / 8; ++s) {
-          const uint32_t ahi = tmem + TC_COL_AV + c * 2 * TC_KV + 8 * s, alo = ahi + TC_KV;
-          const uint64_t bhi = tc_desc(b0 + 256 * s, 128, SBO_V);
-          const uint64_t blo = tc_desc(b0 + TC_BV_BYTES + 256 * s, 128, SBO_V);
-          tc_mma(d, alo, bhi, IDV, s > 0 ? 1u : 0u);
-          tc_mma(d, ahi, blo, IDV, 1u);
-          tc_mma(d, ahi, bhi, IDV, 1u);
-        }
-      }
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(barM)
-                 : "memory");
+    issue(0, false, okB);
+    issue(1, false, okB);
   }
 
   // Face fluxes (CUDA cores, overlapping the volume MMAs), stored over the trace slots.
@@ -360,111 +438,51 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
     }
   }
 
-  // Volume results: derivatives along r, s, t of each own component, chain rule, curl.
-  const bool okM = mbar_wait(barM, 0);
-  bool ok = __syncthreads_and(okM && okB);
+  // Component 0's result, then component 2 into buffer 0; components 1 and 2's results.
+  // Buffer 0 completes phases 0, 1 (volume) and 2, 3 (lift), buffer 1 phases 0 and 1.
+  bool ok = mbar_wait(barM[0], 0);
+  ok = __syncthreads_and(ok && okB);
   tc_fence_after();
-  R phi[3][NP];
-#pragma unroll
-  for (int c = 0; c < 3; ++c)
-#pragma unroll
-    for (int i = 0; i < NP; ++i) phi[c][i] = R(0);
+  if (ok) read_vol(0, 0);
+  store_vol_a(0, 2);
+  ok = handoff(ok);
+  if (tid == 0) issue(0, false, ok);
+  ok = mbar_wait(barM[1], 0) && ok;
+  tc_fence_after();
+  if (ok) read_vol(1, 1);
+  ok = mbar_wait(barM[0], 1) && ok;
+  tc_fence_after();
   if (ok) {
-#pragma unroll
-    for (int cp = 0; cp < 3; ++cp) {
-      // d[tc_vcol(b, i)] = d F_cp / d r_b at node i
-      float d[TC_NV];
-#pragma unroll
-      for (int k0 = 0; k0 < TC_NV; k0 += 16) {
-        float t16[16];
-        tmem_ld16(trow + TC_COL_ACCV + cp * TC_NV + k0, t16);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) d[k0 + k] = t16[k];
-      }
-      // curl F: component 0 = d1 F2 - d2 F1, 1 = d2 F0 - d0 F2, 2 = d0 F1 - d1 F0
-      const int ap = cp == 0 ? 2 : cp == 1 ? 0 : 1;  // axis whose derivative enters with +
-      const int am = cp == 0 ? 1 : cp == 1 ? 2 : 0;  // axis whose derivative enters with -
-      const int cpl = cp == 0 ? 1 : cp == 1 ? 2 : 0;  // output component receiving + d_ap F_cp
-      const int cmi = cp == 0 ? 2 : cp == 1 ? 0 : 1;  // output component receiving - d_am F_cp
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        const R d0 = d[tc_vcol(0, i)], d1 = d[tc_vcol(1, i)], d2 = d[tc_vcol(2, i)];
-        const R dp = G[0 * 3 + ap] * d0 + G[1 * 3 + ap] * d1 + G[2 * 3 + ap] * d2;
-        const R dm = G[0 * 3 + am] * d0 + G[1 * 3 + am] * d1 + G[2 * 3 + am] * d2;
-        phi[cpl][i] += dp;
-        phi[cmi][i] -= dm;
-      }
-    }
+    read_vol(0, 2);
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
       for (int i = 0; i < NP; ++i) phi[c][i] *= sv;
   }
 
-  // Lift A: the fluxes of each output component, split hi / lo, zero-padded to KL columns.
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-#pragma unroll
-    for (int k0 = 0; k0 < TC_KL; k0 += 8) {
-      uint32_t hi[8], lo[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        if (k0 + k < 4 * NFP) {
-          tf32_split(tr[((k0 + k) * 3 + c) * TC_THREADS], hi[k], lo[k]);
-        } else {
-          hi[k] = 0u;
-          lo[k] = 0u;
-        }
-      }
-      tmem_st8(trow + tc_col_al(2 * c) + k0, hi);
-      tmem_st8(trow + tc_col_al(2 * c + 1) + k0, lo);
-    }
-  }
-  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-  tc_fence_before();
-  __syncthreads();
+  // Lift contractions: output components 0 and 1 (buffers 0, 1), then 2 into buffer 0.
+  store_lift_a(0, 0);
+  store_lift_a(1, 1);
+  ok = handoff(ok);
   if (tid == 0) {
-    tc_fence_after();
-    if (ok) {
-      const uint32_t b0 = smem_addr(sB) + 2 * TC_BV_BYTES;
-      constexpr uint32_t SBO_L = (TC_KL / 4) * 128;
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const uint32_t d = tmem + TC_COL_ACCL + c * TC_NL;
-#pragma unroll
-        for (int s = 0; s < TC_KL / 8; ++s) {
-          const uint32_t ahi = tmem + tc_col_al(2 * c) + 8 * s, alo = tmem + tc_col_al(2 * c + 1) + 8 * s;
-          const uint64_t bhi = tc_desc(b0 + 256 * s, 128, SBO_L);
-          const uint64_t blo = tc_desc(b0 + TC_BL_BYTES + 256 * s, 128, SBO_L);
-          tc_mma(d, alo, bhi, IDL, s > 0 ? 1u : 0u);
-          tc_mma(d, ahi, blo, IDL, 1u);
-          tc_mma(d, ahi, bhi, IDL, 1u);
-        }
-      }
-    }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(barM)
-                 : "memory");
+    issue(0, true, ok);
+    issue(1, true, ok);
   }
-  ok = __syncthreads_and(ok && mbar_wait(barM, 1));
+  ok = mbar_wait(barM[0], 0) && ok;
   tc_fence_after();
-  if (ok) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      float l[TC_NL];
-#pragma unroll
-      for (int k0 = 0; k0 < TC_NL; k0 += 16) {
-        float t16[16];
-        tmem_ld16(trow + TC_COL_ACCL + c * TC_NL + k0, t16);
-#pragma unroll
-        for (int k = 0; k < 16; ++k) l[k0 + k] = t16[k];
-      }
-#pragma unroll
-      for (int i = 0; i < NP; ++i) phi[c][i] += l[tc_lcol(i)];
-    }
-  }
+  if (ok) read_lift(0, 0);
+  store_lift_a(0, 2);
+  ok = handoff(ok);
+  if (tid == 0) issue(0, true, ok);
+  ok = mbar_wait(barM[1], 1) && ok;
+  tc_fence_after();
+  if (ok) read_lift(1, 1);
+  ok = mbar_wait(barM[0], 1) && ok;
+  tc_fence_after();
+  if (ok) read_lift(0, 2);
   // Free TMEM (every thread's TMEM reads are complete).
   tc_fence_before();
-  __syncthreads();
+  ok = __syncthreads_and(ok);
   if (warp == 0) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TC_COLS));
@@ -483,7 +501,17 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
 #pragma unroll
       for (int n = 0; n < NP; ++n) phi[c][n] -= so * ev[(c * NP + n) * TILE];
   }
-  if (half && a.jre) add_source<R, NP>(phi, a, cf, tile, lane, 0);  // source on the E rows
+  if (half && jpre) {  // source on the E rows: J_re in this thread's slots, J_im in the partner's
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        const int k = (c * NP + n) * TC_THREADS;
+        phi[c][n] += cf.s_cos * js[k] - cf.s_sin * js[k - 1];
+      }
+  } else if (half && a.jre) {
+    add_source<R, NP>(phi, a, cf, tile, lane, 0);
+  }
   if (a.bre) {  // impedance-face data on this thread's output rows (source sweeps only)
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -493,26 +521,7 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
         phi[c][n] += cf.s_cos * a.bre[o] - cf.s_sin * a.bim[o];
       }
   }
-  if (a.fre) {  // forward sweeps only: F += fa U + fb Phi on this thread's output rows
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        const int64_t o = off + (c * NP + n) * TILE;
-        const R u = a.vin[o];
-        a.fre[o] += cf.fa_re * u + cf.fb_re * phi[c][n];
-        a.fim[o] += cf.fa_im * u + cf.fb_im * phi[c][n];
-      }
-  }
-  if (a.acc_out) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        const int64_t o = off + (c * NP + n) * TILE;
-        a.acc_out[o] = acc_s[(c * NP + n) * TC_THREADS] + cf.c_acc * phi[c][n];
-      }
-  }
+  if (a.fre) accumulate_filter<R, NP>(a, cf, phi, off, 0);  // forward sweeps with the filter only
   if (a.out) {
 #pragma unroll
     for (int c = 0; c < 3; ++c)
@@ -525,12 +534,12 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
 }
 
 // Dynamic shared memory of dg_stage_tc: reference matrices, trace slots, base rows,
-// and the accumulator rows of source stages (acc = true).
-constexpr size_t tc_smem(bool acc) {
-  return size_t(TC_B_BYTES) + size_t(TRACE_SLOTS + (acc ? 6 : 3) * NPQ) * TC_THREADS * sizeof(float);
+// and the prefetched source rows of single-frequency source stages (src = true).
+constexpr size_t tc_smem(bool src) {
+  return size_t(TC_B_BYTES) + size_t(TRACE_SLOTS + (src ? 6 : 3) * NPQ) * TC_THREADS * sizeof(float);
 }
 // Resident CTAs per SM that the TMEM columns allow (512 per SM).
-constexpr int TC_MINB = 512 / TC_COLS >= 2 ? 2 : 1;
+constexpr int TC_MINB = 2;
 
 // The MMA operands of the reference matrices, split hi / lo from double, in the
 // core-matrix layout of tc_cm_offset.

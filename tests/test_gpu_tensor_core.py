@@ -10,9 +10,9 @@ sweeps and converged solves 1e-4 (relative (eps, mu)-weighted L2).
 
 Cases span one tetrahedron, ragged tiles (a CTA covers 64 tetrahedra, two
 tiles, of which the last may not exist), PEC and impedance faces, a distorted
-mesh, permittivity jumps, all three orders, source stages of the classic RK
-forms (accumulator rows) with the on-the-fly filter, and a batch whose
-problems meet inside one CTA.
+mesh, permittivity jumps, all three orders, source stages (nested RK form with
+the source combined per stage, source rows prefetched) with the on-the-fly
+filter, and a batch whose problems meet inside one CTA.
 """
 import math
 
