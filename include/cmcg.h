@@ -466,7 +466,10 @@ int cmcg_set_conductivity(cmcg_handle* h, int problem, const double* sigma);
 /* Limiting-amplitude baseline ("full wave", FW, Section 6): marches the
  * scheme with the time-harmonic source from rest for `periods` periods,
  * U = P_{psi,w}^periods 0, then returns the filtered field F_{psi,w} U of one
- * further period (Section 2.1).  Cost: periods + 1 source sweeps; no CG.  By
+ * further period (Section 2.1).  The source is T-periodic, so P_{psi,w} U =
+ * P_w U + P_{psi,w} 0: the march runs as one source sweep, then one source-free
+ * sweep and one vector addition per further period (equal up to rounding).
+ * Cost: periods + 1 sweeps, two of them with the source; no CG.  By
  * the limiting amplitude principle (Section 1) the result tends to the CMCG
  * result as periods grows when transients decay.  periods >= 0; buffers as in
  * cmcg_solve.  cmcg_fw_solve_batch runs every problem of a batch handle

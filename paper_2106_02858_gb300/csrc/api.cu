@@ -1111,14 +1111,21 @@ int slot_round_dev(cmcg_handle* h, double tol, int max_iter, int* done) {
 }
 
 // Limiting amplitude ("full wave", Section 6): U = P_psi^periods 0, then
-// F_psi U, for every problem of the handle.
+// F_psi U, for every problem of the handle.  The source is T-periodic, so the
+// period map is affine, P_psi U = P U + G with G = P_psi 0: the march is one
+// source sweep, then P U + G per further period (source-free sweeps; G kept in A).
 template <typename R>
 int fw_dev(cmcg_handle* h, int periods, const double* const* j_re, const double* const* j_im, double* const* e_re,
            double* const* e_im, double* const* h_re, double* const* h_im) {
   int rc = set_source<R>(h, j_re, j_im, h->nprob);
   if (rc) return rc;
   CK(cudaMemsetAsync(h->Uw, 0, h->nvec * h->rsize, h->stream));
-  for (int l = 0; l < periods; ++l) sweep_source<R>(h, true, false, nullptr);
+  if (periods > 0) sweep_source<R>(h, true, false, nullptr);
+  if (periods > 1) lincomb<R>(h, h->A, nullptr, nullptr, 1.0, h->Uw, 0.0, nullptr);
+  for (int l = 1; l < periods; ++l) {
+    sweep_free<R>(h, false, nullptr);
+    lincomb<R>(h, h->Uw, nullptr, nullptr, 1.0, h->Uw, 1.0, h->A);
+  }
   CK(cudaMemsetAsync(h->Fre, 0, h->nvec * h->rsize, h->stream));
   CK(cudaMemsetAsync(h->Fim, 0, h->nvec * h->rsize, h->stream));
   sweep_source<R>(h, true, true, nullptr);

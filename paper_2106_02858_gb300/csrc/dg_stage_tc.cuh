@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
   }
 
-  // Own field, neighbour traces, base rows and (source stages) accumulator rows.
+  // Own field, neighbour traces, base rows and (single-frequency source stages) source rows.
   R v[3][NP];
   const int64_t off = tile * VS + cOut * NP * TILE + lane;
 #pragma unroll
