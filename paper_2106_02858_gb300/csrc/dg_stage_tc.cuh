@@ -422,12 +422,13 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
     for (int jf = 0; jf < NFP; ++jf) {
       const int own = FM.v[f][jf];
       R X[3], Y[3];
-      if (interior) {
+      // both jumps formed and one selected: one code path per face node (the trace slots of a
+      // boundary face hold stale values, which the selection discards)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) X[c] = sIn * tr[((f * NFP + jf) * 3 + c) * TC_THREADS] - v[c][own];
-      } else {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) X[c] = bscale * v[c][own];
+      for (int c = 0; c < 3; ++c) {
+        const R xi = sIn * tr[((f * NFP + jf) * 3 + c) * TC_THREADS] - v[c][own];
+        const R xb = bscale * v[c][own];
+        X[c] = interior ? xi : xb;
       }
 #pragma unroll
       for (int c = 0; c < 3; ++c) Y[c] = __shfl_xor_sync(0xffffffffu, X[c], 1);
