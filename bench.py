@@ -355,7 +355,7 @@ def measure_large_request(cmcg, I, hbm_peak):
 
 
 def measure_serving(cmcg, I, rate_hz: float = 150.0, n_small: int = 150, n_large: int = 3, seed: int = 0,
-                    workers: int = 8, max_batch: int = 16, max_wait_ms: float = 5.0):
+                    workers: int = 4, max_batch: int = 32, max_wait_ms: float = 5.0):
     """A Poisson stream through the serving runtime (continuous batching: `workers` threads with
     their own streams, batches of up to `max_batch`): small requests are one P3 source on the
     384-tet cube (the batched-RHS shape), large ones a 12^3-cube P2 problem; latency = submit to
