@@ -34,7 +34,8 @@
 // %globaltimer), after which the CTA records CMCG_ERR_DEVICE_TIMEOUT in a.err,
 // skips the dependent work, frees its TMEM and returns.  TMEM is allocated after
 // the grid-dependency wait, so a CTA that starts early under programmatic
-// dependent launch never holds TMEM while the previous stage still runs.
+// dependent launch never holds TMEM while the previous stage still runs; the
+// bulk copy of the reference matrices is issued before that wait.
 
 constexpr int TC_THREADS = 128;
 constexpr int TC_TETS = 64;
@@ -214,10 +215,8 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
       fk2[f] = gf[(4 + 2 * half) * TILE] * sOut;
     }
   }
-  grid_dep_wait();
-  if (live && a.pactive && !a.pactive[prob]) live = false;  // CG converged (written by the CG kernels)
-  if (!__syncthreads_or(live)) return;
-
+  // The reference matrices (written only at handle creation) are copied before the grid
+  // dependency: one bulk copy, completion counted in bytes on barB.
   const uint32_t barB = smem_addr(&bars[0]);
   const uint32_t barM[2] = {smem_addr(&bars[1]), smem_addr(&bars[2])};
   if (tid == 0) {
@@ -225,7 +224,6 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barM[0]));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(barM[1]));
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-    // the reference matrices: one bulk copy, completion counted in bytes on barB
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(barB), "r"(TC_B_BYTES) : "memory");
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
@@ -233,6 +231,13 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
         "l"(gTcB), "r"(TC_B_BYTES), "r"(barB)
         : "memory");
   }
+  grid_dep_wait();
+  if (live && a.pactive && !a.pactive[prob]) live = false;  // CG converged (written by the CG kernels)
+  if (!__syncthreads_or(live)) {
+    if (tid == 0) mbar_wait(barB, 0);  // the copy lands before the CTA's shared memory is released
+    return;
+  }
+
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
                  "r"(TC_COLS));
