@@ -420,7 +420,8 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
 #pragma unroll
   for (int f = 0; f < 4; ++f) {
     const R n0 = fn[f][0], n1 = fn[f][1], n2 = fn[f][2];
-    const R k1 = fk1[f], k2 = fk2[f];
+    const R k2 = fk2[f];
+    const R m0 = fk1[f] * n0, m1 = fk1[f] * n1, m2 = fk1[f] * n2;  // k1 n, once per face
     const bool interior = code[f] >= 0;
     const R bscale = code[f] == NBR_PEC ? pec : R(-1);
 #pragma unroll
@@ -438,9 +439,9 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
 #pragma unroll
       for (int c = 0; c < 3; ++c) Y[c] = __shfl_xor_sync(0xffffffffu, X[c], 1);
       const R nY = n0 * Y[0] + n1 * Y[1] + n2 * Y[2];
-      tr[((f * NFP + jf) * 3 + 0) * TC_THREADS] = k1 * (n1 * X[2] - n2 * X[1]) + k2 * (Y[0] - n0 * nY);
-      tr[((f * NFP + jf) * 3 + 1) * TC_THREADS] = k1 * (n2 * X[0] - n0 * X[2]) + k2 * (Y[1] - n1 * nY);
-      tr[((f * NFP + jf) * 3 + 2) * TC_THREADS] = k1 * (n0 * X[1] - n1 * X[0]) + k2 * (Y[2] - n2 * nY);
+      tr[((f * NFP + jf) * 3 + 0) * TC_THREADS] = (m1 * X[2] - m2 * X[1]) + k2 * (Y[0] - n0 * nY);
+      tr[((f * NFP + jf) * 3 + 1) * TC_THREADS] = (m2 * X[0] - m0 * X[2]) + k2 * (Y[1] - n1 * nY);
+      tr[((f * NFP + jf) * 3 + 2) * TC_THREADS] = (m0 * X[1] - m1 * X[0]) + k2 * (Y[2] - n2 * nY);
     }
   }
 
