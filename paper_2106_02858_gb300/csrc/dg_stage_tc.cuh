@@ -365,6 +365,8 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
 #pragma unroll
     for (int i = 0; i < NP; ++i) phi[c][i] = R(0);
   // Volume result of own component cp (buffer b): derivatives along r, s, t, chain rule, curl.
+#pragma unroll
+  for (int m = 0; m < 9; ++m) G[m] *= sv;  // the material factor of Phi, folded into the chain rule
   auto read_vol = [&](int b, int cp) {
     float d[TC_NV];
 #pragma unroll
@@ -379,13 +381,12 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
     const int am = cp == 0 ? 1 : cp == 1 ? 2 : 0;   // axis whose derivative enters with -
     const int cpl = cp == 0 ? 1 : cp == 1 ? 2 : 0;  // output component receiving + d_ap F_cp
     const int cmi = cp == 0 ? 2 : cp == 1 ? 0 : 1;  // output component receiving - d_am F_cp
+    // (G carries the material factor sv; each derivative is accumulated into Phi as an FMA chain)
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       const R d0 = d[tc_vcol(0, i)], d1 = d[tc_vcol(1, i)], d2 = d[tc_vcol(2, i)];
-      const R dp = G[0 * 3 + ap] * d0 + G[1 * 3 + ap] * d1 + G[2 * 3 + ap] * d2;
-      const R dm = G[0 * 3 + am] * d0 + G[1 * 3 + am] * d1 + G[2 * 3 + am] * d2;
-      phi[cpl][i] += dp;
-      phi[cmi][i] -= dm;
+      phi[cpl][i] = fmaf(G[2 * 3 + ap], d2, fmaf(G[1 * 3 + ap], d1, fmaf(G[0 * 3 + ap], d0, phi[cpl][i])));
+      phi[cmi][i] = fmaf(-G[2 * 3 + am], d2, fmaf(-G[1 * 3 + am], d1, fmaf(-G[0 * 3 + am], d0, phi[cmi][i])));
     }
   };
   auto read_lift = [&](int b, int c) {
@@ -461,10 +462,6 @@ __global__ void __launch_bounds__(TC_THREADS, MINB) dg_stage_tc(const StageArgs<
   tc_fence_after();
   if (ok) {
     read_vol(0, 2);
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-      for (int i = 0; i < NP; ++i) phi[c][i] *= sv;
   }
 
   // Lift contractions: output components 0 and 1 (buffers 0, 1), then 2 into buffer 0.
