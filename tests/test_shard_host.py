@@ -78,6 +78,28 @@ def test_slab_partition_and_plans(lib, nparts, axis):
         assert np.array_equal(pl["local_tags"][:pl["n_owned"]], p.mesh.tags[own])
 
 
+def test_plans_of_an_arbitrary_partition_and_of_one_part(lib):
+    """The plan does not rely on slabs: a seeded random partition (parts interleaved, many cut
+    faces, some parts without a cut face to a given other part) gives the same invariants, and a
+    single part owns the whole mesh with no ghosts."""
+    p, m = _mesh(lib)
+    nb = _face_neighbours(p.mesh.tets)
+    nparts = 4
+    part = np.random.default_rng(11).integers(0, nparts, p.nt).astype(np.int32)
+    plans = [lib.cmcg_shard_plan(m, part, nparts, q) for q in range(nparts)]
+    for q, pl in enumerate(plans):
+        own = pl["global_of_local"][:pl["n_owned"]]
+        ghosts = pl["global_of_local"][pl["n_owned"]:]
+        assert np.array_equal(own, np.flatnonzero(part == q))
+        assert list(ghosts) == sorted({k2 for k in own for k2 in nb[k] if part[k2] != q})
+        for g, o, ol in zip(ghosts, pl["ghost_owner_part"], pl["ghost_owner_local"]):
+            assert part[g] == o and plans[o]["global_of_local"][ol] == g
+    one = lib.cmcg_shard_plan(m, np.zeros(p.nt, dtype=np.int32), 1, 0)
+    assert one["n_owned"] == p.nt and len(one["global_of_local"]) == p.nt
+    assert np.array_equal(one["global_of_local"], np.arange(p.nt))
+    assert np.array_equal(one["local_tags"], p.mesh.tags)
+
+
 def test_local_operator_equals_global_operator_on_owned_tetrahedra(lib):
     from oracle.dg import apply_B, inner
     from oracle.geometry import build_geometry
